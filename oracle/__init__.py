@@ -1,0 +1,22 @@
+"""Plain, slow FP64 CPU oracle for AGCA multigrid on Kuhn tetrahedral grids.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call,
+link or execute this package; only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg use it.  It shares no code with the CUDA
+library and derives every quantity its own way (geometry from vertex
+coordinates, barycentric inversion, centroid containment, explicit sparse
+matrices, library factorizations).
+
+Modules:
+  mesh      Kuhn meshes, geometry, parent/child maps, interpolation (Sec. 2, Eq. 2.2, Eq. 2.4)
+  fem       element matrices and global assembly of Eqs. 3.4-3.5
+  agca      viscosity hierarchy, flags, element-wise Galerkin (Eqs. 2.6-2.9), V-cycle
+  stokes    Stokes operator, MINRES (Remark 6), direct solve, adjoint gradient
+  pointwise per-vertex rows of the fine operator for sampled checks at large sizes
+
+Parity status: every function here is pinned by tests/test_oracle_*.py
+(closed forms, invariants, brute force, library routines, convergence rates),
+except the iteration counts of the preconditioned solve, which the paper
+prints only as figures (parity unpinned for iteration counts; the solutions
+themselves are pinned against a sparse direct solve).
+"""

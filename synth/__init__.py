@@ -1,0 +1,20 @@
+"""Seeded synthetic inputs for the AGCA Stokes sinker problems.
+
+This package is shared by the CUDA path's tests/bench and by the CPU oracle.
+It holds no arithmetic of the multigrid method itself: it only evaluates the
+analytic viscosity and forcing fields of the sinker benchmarks (Section 3.2,
+Eqs. 3.6-3.12) at element quadrature points and averages them per element.
+"""
+from .sinkers import (  # noqa: F401
+    PERMS,
+    CONFIG_SEED0,
+    Problem,
+    element_quadrature_points,
+    cube_sinker,
+    sphere_sinkers,
+    gaussian_logbumps,
+    batch_problems,
+    adjoint_problem,
+    random_vector,
+    velocity_grid,
+)
