@@ -1,0 +1,185 @@
+/*
+ * agca.h — C ABI of the GB300 (sm_103a) AGCA multigrid library.
+ *
+ * Adaptive Galerkin coarse-grid approximation (AGCA) multigrid for the
+ * generalized variable-viscosity Stokes problem of arXiv 2511.13109:
+ *   -div(2 eta eps(u)) + grad p = f,  -div u = 0 in the unit cube, u = 0 on
+ *   the boundary (Eq. 3.1), discretized with the P1-iso-P2 / P1 pair (Eq. 3.3)
+ *   on uniformly refined Kuhn tetrahedral grids (Eq. 2.2).
+ *
+ * Grid and vector conventions (every pointer argument below follows them):
+ *  - N pressure cubes per axis; the velocity grid has n_L = 2N cubes per axis.
+ *    Level l = 1 (coarsest) .. L (finest) has n_l = n_L / 2^(L-l) cubes per
+ *    axis, V_l = (n_l+1)^3 vertices and E_l = 6 n_l^3 tetrahedra.
+ *  - Vertex id = i + (n+1)*(j + (n+1)*k).  Cube id = i + n*(j + n*k); cube
+ *    (i,j,k) is split along its main diagonal into 6 tetrahedra, type t being
+ *    the t-th permutation p of (0,1,2) in lexicographic order, with local
+ *    vertices v0 = origin, v1 = v0 + e_p0, v2 = v1 + e_p1, v3 = v0 + (1,1,1).
+ *    Element id = 6*cube_id + t.
+ *  - Velocity vectors are SoA: value of component c at vertex v is x[c*V + v],
+ *    boundary vertices included.  Boundary entries of inputs are ignored;
+ *    boundary entries of outputs are written as 0 (homogeneous Dirichlet).
+ *  - Stokes vectors x = [u; p] hold 3*V_L velocity values followed by the
+ *    (N+1)^3 pressure values of the level-(L-1) grid.
+ *  - Local element DoF (vertex a, component c) has index c*4 + a; stored
+ *    Galerkin matrices are 12x12 row-major in that index.
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller.  The
+ * library allocates no device memory: the caller queries the workspace size,
+ * allocates it (e.g. a torch uint8 tensor) and binds it; the size of the
+ * Galerkin store is only known after flagging and is bound separately.
+ * All calls run on the CUDA stream given at creation and are asynchronous,
+ * except agca_flag, agca_setup, agca_solve, agca_adjoint_gradient,
+ * agca_level_info, which synchronize that stream before returning.
+ *
+ * Errors: every call returns an agca_status; the library never aborts or
+ * traps.  agca_last_error() gives a message for the last failing call on a
+ * context.  A context is not thread safe.
+ */
+#ifndef AGCA_H_
+#define AGCA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct agca_ctx agca_ctx;
+
+typedef enum {
+  AGCA_OK = 0,
+  AGCA_EINVAL = 1,     /* bad argument (size, level, null pointer, NaN/<=0 viscosity) */
+  AGCA_ENOMEM = 2,     /* bound workspace or Galerkin store too small */
+  AGCA_ECUDA = 3,      /* a CUDA runtime call failed */
+  AGCA_ENOTCONV = 4,   /* solver stopped at maxit above the tolerance */
+  AGCA_ETIMEOUT = 5,   /* a bounded device wait gave up */
+  AGCA_EINTERNAL = 6,  /* device-detected inconsistency (e.g. non-SPD coarsest matrix) */
+  AGCA_ESTATE = 7      /* call out of order (e.g. apply before setup) */
+} agca_status;
+
+typedef enum { AGCA_FP64 = 0, AGCA_MIXED = 1 } agca_precision;
+typedef enum { AGCA_F64 = 0, AGCA_F32 = 1 } agca_dtype;
+
+/* Level data fields for agca_get_level_data. */
+typedef enum {
+  AGCA_FIELD_MEAN = 0,   /* double[E_l]: element viscosity (finest) or child mean (coarse) */
+  AGCA_FIELD_MAX = 1,    /* double[E_l]: max finest viscosity under the element */
+  AGCA_FIELD_MIN = 2,    /* double[E_l]: min finest viscosity under the element */
+  AGCA_FIELD_FLAGS = 3,  /* uint8[E_l]: 1 if Galerkin-coarsened */
+  AGCA_FIELD_LIST = 4,   /* int32[n_flag]: flagged element ids, ascending */
+  AGCA_FIELD_GCA = 5,    /* double[n_flag*144]: stored Galerkin matrices, list order */
+  AGCA_FIELD_DIAG = 6,   /* double[3*V_l]: diagonal of the level operator (0 on boundary) */
+  AGCA_FIELD_COARSE = 7, /* double[m*m]: dense coarsest operator on interior DoFs (level 1 only) */
+  AGCA_FIELD_PMASS = 8   /* double[(N+1)^3]: viscosity-weighted lumped pressure mass (level L-1) */
+} agca_field;
+
+typedef struct {
+  int n;            /* cubes per axis */
+  int64_t vertices; /* V_l */
+  int64_t elements; /* E_l */
+  int64_t n_flag;   /* flagged elements (0 on the finest level) */
+  double lambda;    /* power-iteration estimate of lambda_max(D^-1 A_l) (0 on level 1) */
+} agca_level_info_t;
+
+/* Human-readable name of a status code (static string). */
+const char* agca_status_string(agca_status s);
+
+/* Create a context for a velocity grid of 2N cubes per axis with n_levels
+ * levels (2N must be divisible by 2^(n_levels-1) with at least 2 cubes per
+ * axis on level 1).  prec selects the V-cycle precision: AGCA_FP64, or
+ * AGCA_MIXED (FP32 smoothing, transfers and coarse applies; FP64 Galerkin
+ * assembly, coarsest solve and Krylov recurrence).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  Host-only; *out is owned by
+ * the caller and released with agca_destroy. */
+agca_status agca_create(int N, int n_levels, int prec, void* cuda_stream, agca_ctx** out);
+void agca_destroy(agca_ctx* ctx);
+const char* agca_last_error(const agca_ctx* ctx);
+
+/* Smoother parameters (Section 4: Chebyshev smoother on D^-1 A): polynomial
+ * degree, interval [lo, hi] * lambda_hat and the number of power iterations
+ * for lambda_hat.  Defaults 2, 0.3, 1.2, 20.  Call before agca_setup. */
+agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, int power_iters);
+
+/* Bytes of device workspace the context needs (excluding the Galerkin store). */
+agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes);
+/* Bind caller-owned device memory of at least agca_workspace_size bytes,
+ * 256-byte aligned.  The memory must outlive the context's use. */
+agca_status agca_bind_workspace(agca_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Copy the finest element viscosities eta (double[E_L], device) into the
+ * workspace.  Every value must be finite and > 0 (checked on the device at
+ * agca_flag: AGCA_EINVAL otherwise).  Eq. 3.5: only the element mean of eta
+ * enters a P1 element matrix (Remark 3). */
+agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev);
+
+/* Build the viscosity hierarchy (per coarse element: mean, max and min over
+ * its 8 children) and flag elements with max > nu * min for Galerkin
+ * coarsening (element-wise form of Eq. 2.8); compact the flagged elements of
+ * every coarse level in ascending id order.  Returns in *gca_bytes the size
+ * of the Galerkin store to bind next.  Synchronizes. */
+agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes);
+/* Bind caller-owned device memory for the stored Galerkin matrices. */
+agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Assemble the local Galerkin matrices of all flagged elements, finest to
+ * coarsest (Eqs. 2.6-2.7, Eq. B.2), the level diagonals, lambda_hat per level,
+ * the dense Cholesky factor of the coarsest operator and the pressure mass.
+ * Synchronizes. */
+agca_status agca_setup(agca_ctx* ctx);
+
+/* y = A_l x for level l (Eq. 2.3 at l = L; the heterogeneous AGCA operator of
+ * Eq. 2.9 for l < L).  dtype AGCA_F64 uses the FP64 data; AGCA_F32 (mixed
+ * contexts only) the FP32 data.  x, y: dtype[3*V_l]. */
+agca_status agca_apply(agca_ctx* ctx, int level, int dtype, const void* x_dev, void* y_dev);
+/* r_c = P^T r_f from level l to l-1 (linear interpolation transpose, Sec. 2.1);
+ * boundary rows of r_c are 0.  r_f: dtype[3*V_l], r_c: dtype[3*V_{l-1}]. */
+agca_status agca_restrict(agca_ctx* ctx, int level, int dtype, const void* rf_dev, void* rc_dev);
+/* x_f += P e_c from level l-1 to l. */
+agca_status agca_prolong_add(agca_ctx* ctx, int level, int dtype, const void* ec_dev, void* xf_dev);
+/* One V-cycle z = V(r) on the velocity block from z = 0 (Section 4: Chebyshev
+ * pre/post smoothing, AGCA coarse operators, exact coarsest solve).
+ * r, z: double[3*V_L]; in mixed contexts the cycle runs in FP32. */
+agca_status agca_vcycle(agca_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* Stokes operator y = K x, K = [[A, B^T], [B, 0]] with B = -D,
+ * D_kj = int psi_k div Phi_j (Eqs. 3.4-3.5).  x, y: double[3*V_L + (N+1)^3]. */
+agca_status agca_stokes_apply(agca_ctx* ctx, const double* x_dev, double* y_dev);
+/* Block-diagonal preconditioner z = diag(V-cycle, Pi M^-1 Pi) r with M the
+ * lumped 1/eta-weighted pressure mass and Pi the mean-zero projection. */
+agca_status agca_precondition(agca_ctx* ctx, const double* r_dev, double* z_dev);
+/* Right-hand side b = [f; 0] with f_(a,c) = sum_T |T| fbar_c(T) / 4 for the
+ * element-mean forcing fbar: double[3*E_L] (SoA by component). */
+agca_status agca_load_vector(agca_ctx* ctx, const double* fbar_dev, double* b_dev);
+
+/* Solve K x = b to ||b - K x||_2 <= rtol ||b||_2 on the true FP64 residual:
+ * residual refinement around preconditioned MINRES (Remark 6), at most maxit
+ * MINRES iterations in total.  x is overwritten (initial guess 0); the
+ * pressure is returned with zero mean.  *iters, *relres (host) receive the
+ * iteration count and final relative residual.  Synchronizes.  Returns
+ * AGCA_ENOTCONV if the tolerance was not met. */
+agca_status agca_solve(agca_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
+                       int* iters, double* relres);
+
+/* Element sensitivities g_e = -lambda_e^T (dA_e/dtheta_e) u_e for theta =
+ * log(eta) (the viscous element matrix is linear in eta_e).  lam_u, u:
+ * double[3*V_L]; g: double[E_L]. */
+agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, const double* u_dev,
+                                     double* g_dev);
+/* Adjoint gradient of J(u) w.r.t. theta = log(eta): solves K lambda =
+ * (dJ/du, 0) with the same preconditioned solver (K is symmetric) to rtol,
+ * then g = agca_element_sensitivity(lambda_u, u).  x: the forward solution
+ * [u; p]; dJdu: double[3*V_L]; g: double[E_L].  Synchronizes. */
+agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const double* dJdu_dev,
+                                  double* g_dev, double rtol, int maxit, int* iters);
+
+/* Level metadata (host struct).  Synchronizes. */
+agca_status agca_level_info(agca_ctx* ctx, int level, agca_level_info_t* out);
+/* Copy a level field (agca_field) into caller device memory. */
+agca_status agca_get_level_data(agca_ctx* ctx, int level, int field, void* dst_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGCA_H_ */

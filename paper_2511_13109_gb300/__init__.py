@@ -1,0 +1,27 @@
+"""GB300-native AGCA multigrid (arXiv 2511.13109): adaptive Galerkin
+coarse-grid approximation for the variable-viscosity Stokes problem.
+
+The compute path is libagca (hand-written CUDA for sm_103a) behind the C ABI
+of include/agca.h; this package is its thin ctypes binding plus a
+torch.autograd.Function for the adjoint gradient.
+"""
+from .agca import (  # noqa: F401
+    F32,
+    F64,
+    FIELD_COARSE,
+    FIELD_DIAG,
+    FIELD_FLAGS,
+    FIELD_GCA,
+    FIELD_LIST,
+    FIELD_MAX,
+    FIELD_MEAN,
+    FIELD_MIN,
+    FIELD_PMASS,
+    FP64,
+    MIXED,
+    AgcaError,
+    Context,
+    default_levels,
+    exported_symbols,
+    lib,
+)

@@ -1,0 +1,159 @@
+// Internal declarations shared by the CUDA translation units of libagca.
+//
+// Kuhn grid conventions (the same as include/agca.h): tetrahedron t of a cube
+// follows the t-th lexicographic permutation p of (0,1,2); its local vertices
+// lie on the cube corners 0, 1<<p0, (1<<p0)|(1<<p1), 7 (corner bit m = offset
+// along axis m).  The barycentric gradients on a cube of size h are g = G/h
+// with G_0 = -e_p0, G_1 = e_p0 - e_p1, G_2 = e_p1 - e_p2, G_3 = e_p2 and the
+// volume is h^3/6, so the viscous element matrix of Eq. 3.5,
+//   [A_e]_{(a,c),(b,d)} = eta_e |T| (delta_cd g_a.g_b + g_{a,d} g_{b,c}),
+// equals eta_e * (h/6) * K'_t with K'_t = delta_cd G_a.G_b + G_{a,d} G_{b,c},
+// an integer matrix.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/agca.h"
+
+namespace agca {
+
+// ---------------------------------------------------------------- Kuhn tables
+__host__ __device__ constexpr int perm(int t, int k) {
+  return t == 0   ? (k == 0 ? 0 : k == 1 ? 1 : 2)
+         : t == 1 ? (k == 0 ? 0 : k == 1 ? 2 : 1)
+         : t == 2 ? (k == 0 ? 1 : k == 1 ? 0 : 2)
+         : t == 3 ? (k == 0 ? 1 : k == 1 ? 2 : 0)
+         : t == 4 ? (k == 0 ? 2 : k == 1 ? 0 : 1)
+                  : (k == 0 ? 2 : k == 1 ? 1 : 0);
+}
+// cube corner (bits x,y,z) of local vertex a of a type-t tetrahedron
+__host__ __device__ constexpr int tet_corner(int t, int a) {
+  return a == 0 ? 0 : a == 1 ? (1 << perm(t, 0)) : a == 2 ? ((1 << perm(t, 0)) | (1 << perm(t, 1))) : 7;
+}
+// component m of the scaled gradient G_a of local vertex a (values -1, 0, 1)
+__host__ __device__ constexpr int kuhn_grad(int t, int a, int m) {
+  return a == 0   ? -(perm(t, 0) == m)
+         : a == 1 ? (perm(t, 0) == m) - (perm(t, 1) == m)
+         : a == 2 ? (perm(t, 1) == m) - (perm(t, 2) == m)
+                  : (perm(t, 2) == m);
+}
+// K'_t entry for local DoFs r = c*4+a, s = d*4+b
+__host__ __device__ constexpr int kuhn_kprime(int t, int r, int s) {
+  return ((r >> 2) == (s >> 2) ? (kuhn_grad(t, r & 3, 0) * kuhn_grad(t, s & 3, 0) +
+                                  kuhn_grad(t, r & 3, 1) * kuhn_grad(t, s & 3, 1) +
+                                  kuhn_grad(t, r & 3, 2) * kuhn_grad(t, s & 3, 2))
+                               : 0) +
+         kuhn_grad(t, r & 3, s >> 2) * kuhn_grad(t, s & 3, r >> 2);
+}
+// local index a of cube corner q in tetrahedron t, or -1
+__host__ __device__ constexpr int corner_local(int t, int q) {
+  return q == 0 ? 0 : q == 7 ? 3 : q == tet_corner(t, 1) ? 1 : q == tet_corner(t, 2) ? 2 : -1;
+}
+
+// Refinement tables, built once on the host from the Kuhn ordering rule and
+// passed to kernels by value (kernel-parameter constant bank; see tables.cu):
+//  child[t][k] = {ox, oy, oz, t'}: k-th child (ascending fine element id) of a
+//                type-t parent: fine cube 2*C + o, fine type t'.
+//  pk2[t][k][i][j] = 2 * lambda_j(parent) at local vertex i of child k.
+struct RefineTables {
+  int8_t child[6][8][4];
+  int8_t pk2[6][8][4][4];
+};
+void build_refine_tables(RefineTables* out);
+const RefineTables& refine_tables();
+
+// ---------------------------------------------------------------- level views
+template <typename T>
+struct LevelOp {
+  int n;               // cubes per axis
+  T h6;                // h / 6
+  T hq;                // h^2 / 6 (divergence terms, finest level)
+  const T* coef;       // per-element coefficient: eta (finest) or child mean (coarse)
+  const int32_t* fidx; // compact Galerkin index per element or -1; nullptr on finest
+  const T* gca;        // stored Galerkin matrices (n_flag * 144)
+  const T* gscale;     // per flagged element scale (mixed) or nullptr
+};
+
+__host__ __device__ inline int64_t nverts(int n) { return (int64_t)(n + 1) * (n + 1) * (n + 1); }
+__host__ __device__ inline int64_t nelems(int n) { return (int64_t)6 * n * n * n; }
+
+// ---------------------------------------------------------------- launchers
+enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_CHEB_FIRST = 2, ST_CHEB_STEP = 3, ST_CHEB_PRE = 4, ST_STOKES = 5 };
+
+template <typename T>
+struct StencilArgs {
+  const T* x;      // input field (ST_CHEB_PRE: unused)
+  const T* b;      // right-hand side (RESID, CHEB*)
+  const T* invD;   // inverse diagonal (CHEB*)
+  const T* xprev;  // previous iterate (CHEB_STEP), may alias out
+  const T* q;      // fine-grid pressure P p (STOKES)
+  T* out;
+  T* out2;         // B_f u on the fine grid (STOKES)
+  T s0, s1, s2;    // mode scalars
+};
+
+// TS: storage type of the vectors; T: compute type (and type of the level data)
+template <typename TS, typename T>
+cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s);
+
+// grid transfers (transfer.cu)
+template <typename T>
+cudaError_t launch_restrict(int nf, int ncomp, bool mask, T scale, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(int nf, int ncomp, bool mask, bool add, const T* ec, T* xf, cudaStream_t s);
+
+// setup kernels (setup.cu)
+cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStream_t s);
+cudaError_t launch_coarsen(int nc, const double* mean_f, const double* mx_f, const double* mn_f, double nu,
+                           double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s);
+cudaError_t launch_compact(const uint8_t* flags, int64_t n, int32_t* fidx, int32_t* list, int32_t* block_counts,
+                           int64_t* total, cudaStream_t s);
+int64_t compact_scratch_blocks(int64_t n);
+cudaError_t launch_galerkin(int nc, int64_t n_flag, const int32_t* list, int nf, bool child_finest,
+                            const double* coef_f, const int32_t* fidx_f, const double* gca_f, double* gca_c,
+                            cudaStream_t s);
+cudaError_t launch_diag(const LevelOp<double>& op, double* diag, double* invD64, float* invD32, cudaStream_t s);
+cudaError_t launch_gca_to_f32(int64_t n_flag, const int32_t* list, const double* mx, const double* gca64,
+                              float* gca32, float* scale32, cudaStream_t s);
+cudaError_t launch_d2f(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_f2d(const float* in, double* out, int64_t n, cudaStream_t s);
+cudaError_t launch_coarse_assemble(const LevelOp<double>& op, double* dense, cudaStream_t s);
+cudaError_t launch_cholesky(double* a, int m, int* status, cudaStream_t s);
+cudaError_t launch_trinv(const double* l, int m, double* linv_cm, double* linv_rm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(int n, const double* linv_cm, const double* linv_rm, const T* r, T* z,
+                                cudaStream_t s);
+cudaError_t launch_pressure_mass(int np, const double* eta_f, double* pmass, double* pmass_inv, cudaStream_t s);
+cudaError_t launch_start_vector(int n, double* v, cudaStream_t s);
+
+// Stokes / Krylov kernels (krylov.cu)
+// device-resident MINRES scalar slots
+enum MinresSlot {
+  MS_GAMMA = 0, MS_GAMMA_OLD, MS_ETA, MS_ETA0, MS_C, MS_C_OLD, MS_S, MS_S_OLD, MS_A1, MS_A2, MS_A3, MS_XCOEF,
+  MS_INV_GAMMA_PREV, MS_UPD_SKIP, MS_DONE, MS_ITERS, MS_TOL_ABS, MS_DOT_KZZ, MS_DOT_ZV, MS_TMP0, MS_TMP1, MS_TMP2,
+  MS_COUNT
+};
+enum VecOp { VOP_SUB = 0, VOP_ADD, VOP_COPY, VOP_ZERO, VOP_PDIV, VOP_SUBS, VOP_MUL, VOP_SCALE_RSQRT };
+int dot_blocks();
+// out[j] = scale * sum_i xs[j][i] * ys[j][i] for npairs <= 3, deterministic
+cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
+                        double* out, double scale, cudaStream_t s);
+cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s);
+cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
+                          const double* scal, cudaStream_t s);
+cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s);
+cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, const double* sc,
+                           cudaStream_t s);
+cudaError_t launch_minres_scalars(double* sc, cudaStream_t s);
+cudaError_t launch_minres_update(int64_t n, const double* z, const double* w, double* wold_to_wnew, double* x,
+                                 const double* sc, cudaStream_t s);
+cudaError_t launch_load_vector(int n, const double* fbar, double* b, cudaStream_t s);
+cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s);
+cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
+                               cudaStream_t s);
+
+}  // namespace agca

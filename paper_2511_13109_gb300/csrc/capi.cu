@@ -1,0 +1,836 @@
+// C ABI of libagca (include/agca.h): context, workspace layout, setup
+// sequence, V-cycle and Krylov drivers.  Host code only; every numerical
+// step runs in the kernels of stencil.cu, transfer.cu, setup.cu, krylov.cu.
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "agca_internal.cuh"
+
+using namespace agca;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Level {
+  int n = 0;
+  int64_t V = 0, E = 0;
+  // FP64 data
+  double* mean = nullptr;  // eta on the finest level
+  double* mx = nullptr;    // == mean on the finest level
+  double* mn = nullptr;
+  uint8_t* flags = nullptr;
+  int32_t* fidx = nullptr;
+  int32_t* list = nullptr;
+  int64_t n_flag = 0;
+  double* gca64 = nullptr;
+  double* diag = nullptr;
+  double* invD64 = nullptr;
+  // FP32 copies (mixed)
+  float* mean32 = nullptr;
+  float* invD32 = nullptr;
+  float* gca32 = nullptr;
+  float* gscale32 = nullptr;
+  // V-cycle vectors in the cycle precision: rhs, two iterate buffers, residual
+  void* vb = nullptr;
+  void* vx = nullptr;
+  void* vt = nullptr;
+  void* vr = nullptr;
+  double lambda = 0.0;
+};
+
+enum KVec { KV_VOLD = 0, KV_V, KV_Z, KV_ZNEW, KV_WOLD, KV_W, KV_KZ, KV_R, KV_D, KV_B, KV_ARHS, KV_ALAM, KV_COUNT };
+
+}  // namespace
+
+struct agca_ctx {
+  int N = 0, L = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  int cheb_degree = 2;
+  double cheb_lo = 0.3, cheb_hi = 1.2;
+  int power_iters = 20;
+  std::vector<Level> lev;  // 1..L
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0, ws_need = 0;
+  char* gs = nullptr;
+  size_t gs_bytes = 0, gs_need = 0;
+  // coarsest
+  int mc = 0;
+  double *cdense = nullptr, *cfac = nullptr, *linv_cm = nullptr, *linv_rm = nullptr;
+  // pressure
+  int64_t Vp = 0;
+  double *pmass = nullptr, *pmass_inv = nullptr, *qfine = nullptr, *sfine = nullptr;
+  // krylov
+  int64_t nt = 0;
+  double* kv[KV_COUNT] = {};
+  double* sc = nullptr;
+  double* partials = nullptr;
+  int* status = nullptr;
+  int64_t* totals = nullptr;
+  int32_t* block_counts = nullptr;
+  double nu = 10.0;
+  bool have_eta = false, flagged = false, setup_done = false;
+  std::string err;
+
+  agca_status fail(agca_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  size_t cyc() const { return prec == AGCA_MIXED ? sizeof(float) : sizeof(double); }
+};
+
+#define CK(...)                                                                                      \
+  do {                                                                                               \
+    cudaError_t e_ = (__VA_ARGS__);                                                                  \
+    if (e_ != cudaSuccess)                                                                           \
+      return ctx->fail(AGCA_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+#define CKS(expr)                  \
+  do {                             \
+    agca_status s_ = (expr);       \
+    if (s_ != AGCA_OK) return s_;  \
+  } while (0)
+
+namespace {
+
+// Assigns 256-byte aligned offsets; with base == nullptr it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <typename T>
+  T* take(int64_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (size_t)count * sizeof(T);
+    return p;
+  }
+};
+
+void carve_workspace(agca_ctx* ctx, char* base) {
+  Carver cv(base);
+  const bool mixed = ctx->prec == AGCA_MIXED;
+  int64_t max_coarse_e = 1;
+  for (int l = 1; l <= ctx->L; ++l) {
+    Level& lv = ctx->lev[l];
+    lv.mean = cv.take<double>(lv.E);
+    if (l < ctx->L) {
+      lv.mx = cv.take<double>(lv.E);
+      lv.mn = cv.take<double>(lv.E);
+      lv.flags = cv.take<uint8_t>(lv.E);
+      lv.fidx = cv.take<int32_t>(lv.E);
+      lv.list = cv.take<int32_t>(lv.E);
+      max_coarse_e = std::max(max_coarse_e, lv.E);
+    } else {
+      lv.mx = lv.mean;
+      lv.mn = lv.mean;
+    }
+    if (mixed) lv.mean32 = cv.take<float>(lv.E);
+    lv.diag = cv.take<double>(3 * lv.V);
+    lv.invD64 = cv.take<double>(3 * lv.V);
+    if (mixed) lv.invD32 = cv.take<float>(3 * lv.V);
+    const size_t es = ctx->cyc();
+    lv.vb = cv.take<char>(3 * lv.V * (int64_t)es);
+    lv.vx = cv.take<char>(3 * lv.V * (int64_t)es);
+    lv.vt = cv.take<char>(3 * lv.V * (int64_t)es);
+    lv.vr = cv.take<char>(3 * lv.V * (int64_t)es);
+  }
+  ctx->block_counts = cv.take<int32_t>(compact_scratch_blocks(max_coarse_e) + 1);
+  ctx->totals = cv.take<int64_t>(ctx->L + 1);
+  ctx->status = cv.take<int>(4);
+  ctx->sc = cv.take<double>(64);
+  ctx->partials = cv.take<double>(3 * (int64_t)dot_blocks());
+  const int64_t m2 = (int64_t)ctx->mc * ctx->mc;
+  ctx->cdense = cv.take<double>(m2);
+  ctx->cfac = cv.take<double>(m2);
+  ctx->linv_cm = cv.take<double>(m2);
+  ctx->linv_rm = cv.take<double>(m2);
+  ctx->pmass = cv.take<double>(ctx->Vp);
+  ctx->pmass_inv = cv.take<double>(ctx->Vp);
+  ctx->qfine = cv.take<double>(ctx->lev[ctx->L].V);
+  ctx->sfine = cv.take<double>(ctx->lev[ctx->L].V);
+  for (int i = 0; i < KV_COUNT; ++i) ctx->kv[i] = cv.take<double>(ctx->nt);
+  ctx->ws_need = (cv.off + kAlign - 1) / kAlign * kAlign;
+}
+
+void carve_gca(agca_ctx* ctx, char* base) {
+  Carver cv(base);
+  const bool mixed = ctx->prec == AGCA_MIXED;
+  for (int l = 1; l < ctx->L; ++l) {
+    Level& lv = ctx->lev[l];
+    lv.gca64 = cv.take<double>(std::max<int64_t>(1, lv.n_flag * 144));
+    if (mixed) {
+      lv.gca32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag * 144));
+      lv.gscale32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag));
+    }
+  }
+  ctx->gs_need = (cv.off + kAlign - 1) / kAlign * kAlign;
+}
+
+LevelOp<double> op64(const agca_ctx* ctx, int l) {
+  const Level& lv = ctx->lev[l];
+  LevelOp<double> op{};
+  op.n = lv.n;
+  op.h6 = 1.0 / (6.0 * lv.n);
+  op.hq = 1.0 / (6.0 * (double)lv.n * lv.n);
+  op.coef = lv.mean;
+  if (l < ctx->L) {
+    op.fidx = lv.fidx;
+    op.gca = lv.gca64;
+  }
+  return op;
+}
+
+LevelOp<float> op32(const agca_ctx* ctx, int l) {
+  const Level& lv = ctx->lev[l];
+  LevelOp<float> op{};
+  op.n = lv.n;
+  op.h6 = (float)(1.0 / (6.0 * lv.n));
+  op.hq = (float)(1.0 / (6.0 * (double)lv.n * lv.n));
+  op.coef = lv.mean32;
+  if (l < ctx->L) {
+    op.fidx = lv.fidx;
+    op.gca = lv.gca32;
+    op.gscale = lv.gscale32;
+  }
+  return op;
+}
+
+template <typename T>
+LevelOp<T> level_op(const agca_ctx* ctx, int l);
+template <>
+LevelOp<double> level_op<double>(const agca_ctx* ctx, int l) {
+  return op64(ctx, l);
+}
+template <>
+LevelOp<float> level_op<float>(const agca_ctx* ctx, int l) {
+  return op32(ctx, l);
+}
+
+template <typename T>
+const T* invD_of(const Level& lv);
+template <>
+const double* invD_of<double>(const Level& lv) {
+  return lv.invD64;
+}
+template <>
+const float* invD_of<float>(const Level& lv) {
+  return lv.invD32;
+}
+
+struct Cheb {
+  double theta, delta, sigma;
+};
+Cheb cheb_params(const agca_ctx* ctx, int l) {
+  const double lam = ctx->lev[l].lambda;
+  const double a = ctx->cheb_lo * lam, b = ctx->cheb_hi * lam;
+  Cheb c;
+  c.theta = 0.5 * (b + a);
+  c.delta = 0.5 * (b - a);
+  c.sigma = c.theta / c.delta;
+  return c;
+}
+
+template <typename T>
+agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, const T* xprev, T* out, double s0,
+                    double s1, double s2) {
+  const Level& lv = ctx->lev[l];
+  StencilArgs<T> a{};
+  a.x = x;
+  a.b = b;
+  a.invD = invD_of<T>(lv);
+  a.xprev = xprev;
+  a.out = out;
+  a.s0 = (T)s0;
+  a.s1 = (T)s1;
+  a.s2 = (T)s2;
+  CK(launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
+  return AGCA_OK;
+}
+
+// Chebyshev smoothing of A_l x = b (Section 4).  from_zero: start at x = 0
+// (the result of the first step is staged on the fly); otherwise start at
+// *cur.  cur/other are the two iterate buffers; returns the result buffer.
+template <typename T>
+agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur, T** other) {
+  const Cheb c = cheb_params(ctx, l);
+  const int k = ctx->cheb_degree;
+  double rho = 1.0 / c.sigma;
+  int step = 1;
+  if (from_zero && k == 2) {
+    const double rn = 1.0 / (2.0 * c.sigma - rho);
+    CKS(stencil<T>(ctx, ST_CHEB_PRE, l, nullptr, b, nullptr, *cur, rn * rho, 2.0 * rn / c.delta, 1.0 / c.theta));
+    return AGCA_OK;
+  }
+  if (from_zero) CK(cudaMemsetAsync(*cur, 0, 3 * ctx->lev[l].V * sizeof(T), ctx->stream));
+  // first step: other = cur + D^-1 (b - A cur) / theta
+  CKS(stencil<T>(ctx, ST_CHEB_FIRST, l, *cur, b, nullptr, *other, 1.0 / c.theta, 0.0, 0.0));
+  std::swap(*cur, *other);  // cur = x1, other = x0
+  for (step = 1; step < k; ++step) {
+    const double rn = 1.0 / (2.0 * c.sigma - rho);
+    // x_{i+1} = x_i + rn*rho (x_i - x_{i-1}) + (2 rn / delta) D^-1 (b - A x_i), written over x_{i-1}
+    CKS(stencil<T>(ctx, ST_CHEB_STEP, l, *cur, b, *other, *other, rn * rho, 2.0 * rn / c.delta, 0.0));
+    std::swap(*cur, *other);
+    rho = rn;
+  }
+  return AGCA_OK;
+}
+
+// V-cycle on level l for rhs b; X, Tb are the iterate buffers.  Returns the
+// buffer holding the result in *res.
+template <typename T>
+agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
+  if (l == 1) {
+    CK(launch_coarse_solve<T>(ctx->lev[1].n, ctx->linv_cm, ctx->linv_rm, b, X, ctx->stream));
+    *res = X;
+    return AGCA_OK;
+  }
+  Level& lv = ctx->lev[l];
+  Level& lc = ctx->lev[l - 1];
+  T* cur = X;
+  T* other = Tb;
+  CKS(chebyshev<T>(ctx, l, b, true, &cur, &other));
+  T* r = static_cast<T*>(lv.vr);
+  CKS(stencil<T>(ctx, ST_RESID, l, cur, b, nullptr, r, 0, 0, 0));
+  T* bc = static_cast<T*>(lc.vb);
+  CK(launch_restrict<T>(lv.n, 3, true, T(1), r, bc, ctx->stream));
+  T* ec = nullptr;
+  CKS(cycle<T>(ctx, l - 1, bc, static_cast<T*>(lc.vx), static_cast<T*>(lc.vt), &ec));
+  CK(launch_prolong<T>(lv.n, 3, true, true, ec, cur, ctx->stream));
+  CKS(chebyshev<T>(ctx, l, b, false, &cur, &other));
+  *res = cur;
+  return AGCA_OK;
+}
+
+agca_status vcycle_impl(agca_ctx* ctx, const double* r, double* z) {
+  const int L = ctx->L;
+  Level& lf = ctx->lev[L];
+  const int64_t n3 = 3 * lf.V;
+  if (ctx->prec == AGCA_FP64) {
+    double* res = nullptr;
+    CKS(cycle<double>(ctx, L, r, z, static_cast<double*>(lf.vt), &res));
+    if (res != z) CK(cudaMemcpyAsync(z, res, n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    float* b32 = static_cast<float*>(lf.vb);
+    CK(launch_d2f(r, b32, n3, ctx->stream));
+    float* res = nullptr;
+    CKS(cycle<float>(ctx, L, b32, static_cast<float*>(lf.vx), static_cast<float*>(lf.vt), &res));
+    CK(launch_f2d(res, z, n3, ctx->stream));
+  }
+  return AGCA_OK;
+}
+
+// K x = [A u + B^T p ; B u], B = -P^T B_f, B^T p = -B_f^T (P p)
+template <typename TC>
+agca_status stokes_impl(agca_ctx* ctx, const double* x, double* y) {
+  const int L = ctx->L;
+  const Level& lf = ctx->lev[L];
+  const int64_t n3 = 3 * lf.V;
+  CK(launch_prolong<double>(lf.n, 1, false, false, x + n3, ctx->qfine, ctx->stream));
+  StencilArgs<double> a{};
+  a.x = x;
+  a.q = ctx->qfine;
+  a.out = y;
+  a.out2 = ctx->sfine;
+  CK(launch_stencil<double, TC>(ST_STOKES, level_op<TC>(ctx, L), a, ctx->stream));
+  CK(launch_restrict<double>(lf.n, 1, false, -1.0, ctx->sfine, y + n3, ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status stokes_dispatch(agca_ctx* ctx, const double* x, double* y, bool low) {
+  if (low && ctx->prec == AGCA_MIXED) return stokes_impl<float>(ctx, x, y);
+  return stokes_impl<double>(ctx, x, y);
+}
+
+agca_status precond_impl(agca_ctx* ctx, const double* r, double* z) {
+  const int64_t n3 = 3 * ctx->lev[ctx->L].V;
+  CKS(vcycle_impl(ctx, r, z));
+  const double* rp = r + n3;
+  double* zp = z + n3;
+  const double inv = 1.0 / (double)ctx->Vp;
+  CK(launch_sum(rp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP0, inv, ctx->stream));
+  CK(launch_vec_op(VOP_PDIV, ctx->Vp, zp, rp, ctx->pmass_inv, nullptr, ctx->sc + MS_TMP0, ctx->stream));
+  CK(launch_sum(zp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP1, inv, ctx->stream));
+  CK(launch_vec_op(VOP_SUBS, ctx->Vp, zp, zp, nullptr, nullptr, ctx->sc + MS_TMP1, ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status dot1(agca_ctx* ctx, const double* x, const double* y, int64_t n, double* out_dev) {
+  const double* xs[1] = {x};
+  const double* ys[1] = {y};
+  CK(launch_dots(1, xs, ys, n, ctx->partials, out_dev, 1.0, ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status read_scalar(agca_ctx* ctx, const double* dev, double* host) {
+  CK(cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AGCA_OK;
+}
+
+// Preconditioned MINRES for K d = b from d = 0 until the preconditioned
+// residual norm drops by tol_rel (Remark 6).  low: inner operator applied
+// with FP32 arithmetic in mixed contexts.
+agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_rel, int maxit, bool low,
+                        int* iters) {
+  const int64_t nt = ctx->nt;
+  cudaStream_t s = ctx->stream;
+  double* vold = ctx->kv[KV_VOLD];
+  double* v = ctx->kv[KV_V];
+  double* z = ctx->kv[KV_Z];
+  double* zn = ctx->kv[KV_ZNEW];
+  double* wold = ctx->kv[KV_WOLD];
+  double* w = ctx->kv[KV_W];
+  double* kz = ctx->kv[KV_KZ];
+  CK(launch_vec_op(VOP_ZERO, nt, d, nullptr, nullptr, nullptr, nullptr, s));
+  CK(launch_vec_op(VOP_ZERO, nt, vold, nullptr, nullptr, nullptr, nullptr, s));
+  CK(launch_vec_op(VOP_ZERO, nt, wold, nullptr, nullptr, nullptr, nullptr, s));
+  CK(launch_vec_op(VOP_ZERO, nt, w, nullptr, nullptr, nullptr, nullptr, s));
+  CK(launch_vec_op(VOP_COPY, nt, v, b, nullptr, nullptr, nullptr, s));
+  CKS(precond_impl(ctx, v, z));
+  CKS(dot1(ctx, z, v, nt, ctx->sc + MS_DOT_ZV));
+  CK(launch_minres_init(ctx->sc, tol_rel, s));
+  const int check_every = 4;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    CKS(stokes_dispatch(ctx, z, kz, low));
+    CKS(dot1(ctx, kz, z, nt, ctx->sc + MS_DOT_KZZ));
+    CK(launch_lanczos(nt, kz, v, vold, ctx->sc, s));  // vold <- v_new
+    CKS(precond_impl(ctx, vold, zn));
+    CKS(dot1(ctx, zn, vold, nt, ctx->sc + MS_DOT_ZV));
+    CK(launch_minres_scalars(ctx->sc, s));
+    CK(launch_minres_update(nt, z, w, wold, d, ctx->sc, s));  // wold <- w_new
+    std::swap(vold, v);
+    std::swap(z, zn);
+    std::swap(wold, w);
+    if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+      double done = 0.0;
+      CKS(read_scalar(ctx, ctx->sc + MS_DONE, &done));
+      if (done != 0.0) break;
+    }
+  }
+  double its = 0.0;
+  CKS(read_scalar(ctx, ctx->sc + MS_ITERS, &its));
+  *iters = (int)its;
+  return AGCA_OK;
+}
+
+agca_status project_pressure(agca_ctx* ctx, double* x) {
+  const int64_t n3 = 3 * ctx->lev[ctx->L].V;
+  CK(launch_sum(x + n3, ctx->Vp, ctx->partials, ctx->sc + MS_TMP2, 1.0 / (double)ctx->Vp, ctx->stream));
+  CK(launch_vec_op(VOP_SUBS, ctx->Vp, x + n3, x + n3, nullptr, nullptr, ctx->sc + MS_TMP2, ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol, int maxit, int* iters,
+                       double* relres) {
+  const int64_t nt = ctx->nt;
+  cudaStream_t s = ctx->stream;
+  double* r = ctx->kv[KV_R];
+  double* d = ctx->kv[KV_D];
+  double* kx = ctx->kv[KV_KZ];
+  // Dirichlet rows carry no equation: work on a copy of b with them zeroed
+  double* bm = ctx->kv[KV_B];
+  CK(launch_vec_op(VOP_COPY, nt, bm, b_in, nullptr, nullptr, nullptr, s));
+  CK(launch_mask_boundary(ctx->lev[ctx->L].n, bm, s));
+  const double* b = bm;
+  CK(launch_vec_op(VOP_ZERO, nt, x, nullptr, nullptr, nullptr, nullptr, s));
+  double nb2 = 0.0;
+  CKS(dot1(ctx, b, b, nt, ctx->sc + MS_TMP0));
+  CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nb2));
+  const double nb = sqrt(nb2);
+  int total = 0;
+  double rel = nb > 0.0 ? 1.0 : 0.0;
+  const bool mixed = ctx->prec == AGCA_MIXED;
+  for (int outer = 0; outer < 60 && nb > 0.0; ++outer) {
+    CKS(stokes_dispatch(ctx, x, kx, false));
+    CK(launch_vec_op(VOP_SUB, nt, r, b, kx, nullptr, nullptr, s));
+    double nr2 = 0.0;
+    CKS(dot1(ctx, r, r, nt, ctx->sc + MS_TMP0));
+    CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nr2));
+    rel = sqrt(nr2) / nb;
+    if (!(rel > rtol) || total >= maxit) break;
+    double inner = 0.1 * rtol / rel;
+    if (mixed) inner = std::max(inner, 1e-5);
+    inner = std::max(inner, 1e-14);
+    int its = 0;
+    CKS(minres_impl(ctx, r, d, inner, maxit - total, mixed, &its));
+    total += its;
+    CK(launch_vec_op(VOP_ADD, nt, x, x, d, nullptr, nullptr, s));
+    CKS(project_pressure(ctx, x));
+    if (its == 0) break;
+  }
+  if (iters) *iters = total;
+  if (relres) *relres = rel;
+  if (!(rel <= rtol)) return ctx->fail(AGCA_ENOTCONV, "solver stopped above the tolerance");
+  return AGCA_OK;
+}
+
+agca_status check_status(agca_ctx* ctx, const char* where) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st & 1) return ctx->fail(AGCA_EINVAL, std::string(where) + ": viscosity must be finite and > 0");
+  if (st & 2) return ctx->fail(AGCA_EINTERNAL, std::string(where) + ": coarsest operator is not SPD");
+  return AGCA_OK;
+}
+
+agca_status power_lambda(agca_ctx* ctx, int l, double* lam) {
+  const Level& lv = ctx->lev[l];
+  const int64_t n3 = 3 * lv.V;
+  cudaStream_t s = ctx->stream;
+  double* v = ctx->kv[KV_VOLD];
+  double* w = ctx->kv[KV_V];
+  CK(launch_start_vector(lv.n, v, s));
+  for (int it = 0; it < ctx->power_iters; ++it) {
+    CKS(stencil<double>(ctx, ST_APPLY, l, v, nullptr, nullptr, w, 0, 0, 0));
+    CK(launch_vec_op(VOP_MUL, n3, w, w, lv.invD64, nullptr, nullptr, s));
+    CKS(dot1(ctx, w, w, n3, ctx->sc + MS_TMP0));
+    CK(launch_vec_op(VOP_SCALE_RSQRT, n3, v, w, nullptr, nullptr, ctx->sc + MS_TMP0, s));
+  }
+  CKS(stencil<double>(ctx, ST_APPLY, l, v, nullptr, nullptr, w, 0, 0, 0));
+  CKS(dot1(ctx, v, w, n3, ctx->sc + MS_TMP0));
+  CK(launch_vec_op(VOP_MUL, n3, w, v, lv.diag, nullptr, nullptr, s));
+  CKS(dot1(ctx, v, w, n3, ctx->sc + MS_TMP1));
+  double num = 0.0, den = 0.0;
+  CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &num));
+  CKS(read_scalar(ctx, ctx->sc + MS_TMP1, &den));
+  *lam = num / den;
+  return AGCA_OK;
+}
+
+bool valid_level(const agca_ctx* ctx, int l) { return l >= 1 && l <= ctx->L; }
+
+}  // namespace
+
+extern "C" {
+
+const char* agca_status_string(agca_status s) {
+  switch (s) {
+    case AGCA_OK: return "AGCA_OK";
+    case AGCA_EINVAL: return "AGCA_EINVAL";
+    case AGCA_ENOMEM: return "AGCA_ENOMEM";
+    case AGCA_ECUDA: return "AGCA_ECUDA";
+    case AGCA_ENOTCONV: return "AGCA_ENOTCONV";
+    case AGCA_ETIMEOUT: return "AGCA_ETIMEOUT";
+    case AGCA_EINTERNAL: return "AGCA_EINTERNAL";
+    case AGCA_ESTATE: return "AGCA_ESTATE";
+  }
+  return "unknown";
+}
+
+agca_status agca_create(int N, int n_levels, int prec, void* cuda_stream, agca_ctx** out) {
+  if (!out) return AGCA_EINVAL;
+  *out = nullptr;
+  if (N < 1 || n_levels < 2 || n_levels > 12 || (prec != AGCA_FP64 && prec != AGCA_MIXED)) return AGCA_EINVAL;
+  const int nL = 2 * N;
+  if (nL % (1 << (n_levels - 1)) != 0 || (nL >> (n_levels - 1)) < 2) return AGCA_EINVAL;
+  if (nL > 1024) return AGCA_EINVAL;
+  agca_ctx* ctx = new agca_ctx();
+  ctx->N = N;
+  ctx->L = n_levels;
+  ctx->prec = prec;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->lev.resize(n_levels + 1);
+  for (int l = 1; l <= n_levels; ++l) {
+    Level& lv = ctx->lev[l];
+    lv.n = nL >> (n_levels - l);
+    lv.V = nverts(lv.n);
+    lv.E = nelems(lv.n);
+  }
+  const int n1 = ctx->lev[1].n;
+  ctx->mc = 3 * (n1 - 1) * (n1 - 1) * (n1 - 1);
+  if (ctx->mc > 6000) {  // the coarsest dense factor must stay small
+    delete ctx;
+    return AGCA_EINVAL;
+  }
+  ctx->Vp = nverts(nL / 2);
+  ctx->nt = 3 * ctx->lev[n_levels].V + ctx->Vp;
+  carve_workspace(ctx, nullptr);
+  *out = ctx;
+  return AGCA_OK;
+}
+
+void agca_destroy(agca_ctx* ctx) { delete ctx; }
+
+const char* agca_last_error(const agca_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, int power_iters) {
+  if (!ctx) return AGCA_EINVAL;
+  if (degree < 2 || degree > 8 || !(lo > 0.0) || !(hi > lo) || power_iters < 1 || power_iters > 1000)
+    return ctx->fail(AGCA_EINVAL, "smoother parameters out of range");
+  ctx->cheb_degree = degree;
+  ctx->cheb_lo = lo;
+  ctx->cheb_hi = hi;
+  ctx->power_iters = power_iters;
+  ctx->setup_done = false;
+  return AGCA_OK;
+}
+
+agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return AGCA_EINVAL;
+  *bytes = ctx->ws_need;
+  return AGCA_OK;
+}
+
+agca_status agca_bind_workspace(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx) return AGCA_EINVAL;
+  if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return ctx->fail(AGCA_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < ctx->ws_need) return ctx->fail(AGCA_ENOMEM, "workspace too small");
+  ctx->ws = static_cast<char*>(dev_ptr);
+  ctx->ws_bytes = bytes;
+  carve_workspace(ctx, ctx->ws);
+  ctx->have_eta = ctx->flagged = ctx->setup_done = false;
+  ctx->gs = nullptr;
+  return AGCA_OK;
+}
+
+agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
+  if (!ctx || !eta_dev) return AGCA_EINVAL;
+  if (!ctx->ws) return ctx->fail(AGCA_ESTATE, "bind the workspace first");
+  Level& lf = ctx->lev[ctx->L];
+  CK(cudaMemcpyAsync(lf.mean, eta_dev, lf.E * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->have_eta = true;
+  ctx->flagged = ctx->setup_done = false;
+  return AGCA_OK;
+}
+
+agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
+  if (!ctx || !gca_bytes) return AGCA_EINVAL;
+  if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
+  if (!(nu >= 0.0) || !isfinite(nu)) return ctx->fail(AGCA_EINVAL, "nu must be finite and >= 0");
+  cudaStream_t s = ctx->stream;
+  const int L = ctx->L;
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), s));
+  CK(launch_check_eta(ctx->lev[L].mean, ctx->lev[L].E, ctx->status, s));
+  CKS(check_status(ctx, "agca_flag"));
+  ctx->nu = nu;
+  for (int l = L - 1; l >= 1; --l) {
+    Level& lc = ctx->lev[l];
+    const Level& lf = ctx->lev[l + 1];
+    CK(launch_coarsen(lc.n, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
+  }
+  for (int l = 1; l < L; ++l) {
+    Level& lc = ctx->lev[l];
+    CK(launch_compact(lc.flags, lc.E, lc.fidx, lc.list, ctx->block_counts, ctx->totals + l, s));
+  }
+  std::vector<int64_t> tot(L + 1, 0);
+  CK(cudaMemcpyAsync(tot.data(), ctx->totals, (L + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int l = 1; l < L; ++l) ctx->lev[l].n_flag = tot[l];
+  carve_gca(ctx, nullptr);
+  *gca_bytes = ctx->gs_need;
+  ctx->flagged = true;
+  ctx->setup_done = false;
+  ctx->gs = nullptr;
+  return AGCA_OK;
+}
+
+agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx) return AGCA_EINVAL;
+  if (!ctx->flagged) return ctx->fail(AGCA_ESTATE, "flag first");
+  if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return ctx->fail(AGCA_EINVAL, "store must be 256-byte aligned");
+  if (bytes < ctx->gs_need) return ctx->fail(AGCA_ENOMEM, "Galerkin store too small");
+  ctx->gs = static_cast<char*>(dev_ptr);
+  ctx->gs_bytes = bytes;
+  carve_gca(ctx, ctx->gs);
+  return AGCA_OK;
+}
+
+agca_status agca_setup(agca_ctx* ctx) {
+  if (!ctx) return AGCA_EINVAL;
+  if (!ctx->flagged || !ctx->gs) return ctx->fail(AGCA_ESTATE, "flag and bind the Galerkin store first");
+  cudaStream_t s = ctx->stream;
+  const int L = ctx->L;
+  const bool mixed = ctx->prec == AGCA_MIXED;
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), s));
+  // Galerkin matrices, finest to coarsest (Eq. 2.7)
+  for (int l = L - 1; l >= 1; --l) {
+    Level& lc = ctx->lev[l];
+    const Level& lf = ctx->lev[l + 1];
+    const bool child_finest = (l + 1 == L);
+    CK(launch_galerkin(lc.n, lc.n_flag, lc.list, lf.n, child_finest, lf.mean, child_finest ? nullptr : lf.fidx,
+                       child_finest ? nullptr : lf.gca64, lc.gca64, s));
+  }
+  for (int l = 1; l <= L; ++l) {
+    Level& lv = ctx->lev[l];
+    if (mixed) {
+      CK(launch_d2f(lv.mean, lv.mean32, lv.E, s));
+      if (l < L) CK(launch_gca_to_f32(lv.n_flag, lv.list, lv.mx, lv.gca64, lv.gca32, lv.gscale32, s));
+    }
+    CK(launch_diag(op64(ctx, l), lv.diag, lv.invD64, mixed ? lv.invD32 : nullptr, s));
+  }
+  // coarsest operator: dense assembly, Cholesky, explicit inverse factor
+  CK(launch_coarse_assemble(op64(ctx, 1), ctx->cdense, s));
+  CK(cudaMemcpyAsync(ctx->cfac, ctx->cdense, (size_t)ctx->mc * ctx->mc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(launch_cholesky(ctx->cfac, ctx->mc, ctx->status, s));
+  CK(launch_trinv(ctx->cfac, ctx->mc, ctx->linv_cm, ctx->linv_rm, s));
+  CKS(check_status(ctx, "agca_setup"));
+  for (int l = 2; l <= L; ++l) CKS(power_lambda(ctx, l, &ctx->lev[l].lambda));
+  CK(launch_pressure_mass(ctx->lev[L].n / 2, ctx->lev[L].mean, ctx->pmass, ctx->pmass_inv, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->setup_done = true;
+  return AGCA_OK;
+}
+
+agca_status agca_apply(agca_ctx* ctx, int level, int dtype, const void* x_dev, void* y_dev) {
+  if (!ctx || !x_dev || !y_dev) return AGCA_EINVAL;
+  if (!valid_level(ctx, level)) return ctx->fail(AGCA_EINVAL, "level out of range");
+  if (!ctx->setup_done && !(level == ctx->L && ctx->have_eta && dtype == AGCA_F64))
+    return ctx->fail(AGCA_ESTATE, "setup first");
+  if (dtype == AGCA_F64)
+    return stencil<double>(ctx, ST_APPLY, level, static_cast<const double*>(x_dev), nullptr, nullptr,
+                           static_cast<double*>(y_dev), 0, 0, 0);
+  if (dtype == AGCA_F32 && ctx->prec == AGCA_MIXED)
+    return stencil<float>(ctx, ST_APPLY, level, static_cast<const float*>(x_dev), nullptr, nullptr,
+                          static_cast<float*>(y_dev), 0, 0, 0);
+  return ctx->fail(AGCA_EINVAL, "dtype not available in this context");
+}
+
+agca_status agca_restrict(agca_ctx* ctx, int level, int dtype, const void* rf_dev, void* rc_dev) {
+  if (!ctx || !rf_dev || !rc_dev) return AGCA_EINVAL;
+  if (level < 2 || level > ctx->L) return ctx->fail(AGCA_EINVAL, "level out of range");
+  const int nf = ctx->lev[level].n;
+  if (dtype == AGCA_F64)
+    CK(launch_restrict<double>(nf, 3, true, 1.0, static_cast<const double*>(rf_dev), static_cast<double*>(rc_dev),
+                               ctx->stream));
+  else if (dtype == AGCA_F32)
+    CK(launch_restrict<float>(nf, 3, true, 1.0f, static_cast<const float*>(rf_dev), static_cast<float*>(rc_dev),
+                              ctx->stream));
+  else
+    return ctx->fail(AGCA_EINVAL, "bad dtype");
+  return AGCA_OK;
+}
+
+agca_status agca_prolong_add(agca_ctx* ctx, int level, int dtype, const void* ec_dev, void* xf_dev) {
+  if (!ctx || !ec_dev || !xf_dev) return AGCA_EINVAL;
+  if (level < 2 || level > ctx->L) return ctx->fail(AGCA_EINVAL, "level out of range");
+  const int nf = ctx->lev[level].n;
+  if (dtype == AGCA_F64)
+    CK(launch_prolong<double>(nf, 3, true, true, static_cast<const double*>(ec_dev), static_cast<double*>(xf_dev),
+                              ctx->stream));
+  else if (dtype == AGCA_F32)
+    CK(launch_prolong<float>(nf, 3, true, true, static_cast<const float*>(ec_dev), static_cast<float*>(xf_dev),
+                             ctx->stream));
+  else
+    return ctx->fail(AGCA_EINVAL, "bad dtype");
+  return AGCA_OK;
+}
+
+agca_status agca_vcycle(agca_ctx* ctx, const double* r_dev, double* z_dev) {
+  if (!ctx || !r_dev || !z_dev) return AGCA_EINVAL;
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  return vcycle_impl(ctx, r_dev, z_dev);
+}
+
+agca_status agca_stokes_apply(agca_ctx* ctx, const double* x_dev, double* y_dev) {
+  if (!ctx || !x_dev || !y_dev) return AGCA_EINVAL;
+  if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
+  return stokes_impl<double>(ctx, x_dev, y_dev);
+}
+
+agca_status agca_precondition(agca_ctx* ctx, const double* r_dev, double* z_dev) {
+  if (!ctx || !r_dev || !z_dev) return AGCA_EINVAL;
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  return precond_impl(ctx, r_dev, z_dev);
+}
+
+agca_status agca_load_vector(agca_ctx* ctx, const double* fbar_dev, double* b_dev) {
+  if (!ctx || !fbar_dev || !b_dev) return AGCA_EINVAL;
+  const Level& lf = ctx->lev[ctx->L];
+  CK(launch_load_vector(lf.n, fbar_dev, b_dev, ctx->stream));
+  CK(cudaMemsetAsync(b_dev + 3 * lf.V, 0, ctx->Vp * sizeof(double), ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status agca_solve(agca_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
+                       double* relres) {
+  if (!ctx || !b_dev || !x_dev) return AGCA_EINVAL;
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  if (!(rtol > 0.0) || maxit < 1) return ctx->fail(AGCA_EINVAL, "rtol must be > 0 and maxit >= 1");
+  return solve_impl(ctx, b_dev, x_dev, rtol, maxit, iters, relres);
+}
+
+agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, const double* u_dev, double* g_dev) {
+  if (!ctx || !lam_u_dev || !u_dev || !g_dev) return AGCA_EINVAL;
+  if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
+  const Level& lf = ctx->lev[ctx->L];
+  CK(launch_sensitivity(lf.n, lf.mean, lam_u_dev, u_dev, g_dev, ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const double* dJdu_dev, double* g_dev,
+                                  double rtol, int maxit, int* iters) {
+  if (!ctx || !x_dev || !dJdu_dev || !g_dev) return AGCA_EINVAL;
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  if (!(rtol > 0.0) || maxit < 1) return ctx->fail(AGCA_EINVAL, "rtol must be > 0 and maxit >= 1");
+  const Level& lf = ctx->lev[ctx->L];
+  const int64_t n3 = 3 * lf.V;
+  double* rhs = ctx->kv[KV_ARHS];
+  double* lam = ctx->kv[KV_ALAM];
+  CK(cudaMemcpyAsync(rhs, dJdu_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemsetAsync(rhs + n3, 0, ctx->Vp * sizeof(double), ctx->stream));
+  double rel = 0.0;
+  int its = 0;
+  const agca_status st = solve_impl(ctx, rhs, lam, rtol, maxit, &its, &rel);
+  if (iters) *iters = its;
+  if (st != AGCA_OK) return st;
+  CK(launch_sensitivity(lf.n, lf.mean, lam, x_dev, g_dev, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status agca_level_info(agca_ctx* ctx, int level, agca_level_info_t* out) {
+  if (!ctx || !out) return AGCA_EINVAL;
+  if (!valid_level(ctx, level)) return ctx->fail(AGCA_EINVAL, "level out of range");
+  const Level& lv = ctx->lev[level];
+  out->n = lv.n;
+  out->vertices = lv.V;
+  out->elements = lv.E;
+  out->n_flag = level < ctx->L ? lv.n_flag : 0;
+  out->lambda = lv.lambda;
+  return AGCA_OK;
+}
+
+agca_status agca_get_level_data(agca_ctx* ctx, int level, int field, void* dst_dev) {
+  if (!ctx || !dst_dev) return AGCA_EINVAL;
+  if (!valid_level(ctx, level)) return ctx->fail(AGCA_EINVAL, "level out of range");
+  const Level& lv = ctx->lev[level];
+  const void* src = nullptr;
+  size_t bytes = 0;
+  const bool coarse = level < ctx->L;
+  switch (field) {
+    case AGCA_FIELD_MEAN: src = lv.mean; bytes = lv.E * sizeof(double); break;
+    case AGCA_FIELD_MAX: src = lv.mx; bytes = lv.E * sizeof(double); break;
+    case AGCA_FIELD_MIN: src = lv.mn; bytes = lv.E * sizeof(double); break;
+    case AGCA_FIELD_FLAGS:
+      if (!coarse) return ctx->fail(AGCA_EINVAL, "no flags on the finest level");
+      src = lv.flags; bytes = lv.E; break;
+    case AGCA_FIELD_LIST:
+      if (!coarse) return ctx->fail(AGCA_EINVAL, "no flags on the finest level");
+      src = lv.list; bytes = lv.n_flag * sizeof(int32_t); break;
+    case AGCA_FIELD_GCA:
+      if (!coarse || !ctx->setup_done) return ctx->fail(AGCA_ESTATE, "no Galerkin matrices here");
+      src = lv.gca64; bytes = lv.n_flag * 144 * sizeof(double); break;
+    case AGCA_FIELD_DIAG:
+      if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+      src = lv.diag; bytes = 3 * lv.V * sizeof(double); break;
+    case AGCA_FIELD_COARSE:
+      if (level != 1 || !ctx->setup_done) return ctx->fail(AGCA_ESTATE, "coarse matrix: level 1 after setup");
+      src = ctx->cdense; bytes = (size_t)ctx->mc * ctx->mc * sizeof(double); break;
+    case AGCA_FIELD_PMASS:
+      if (level != ctx->L - 1 || !ctx->setup_done) return ctx->fail(AGCA_ESTATE, "pressure mass: level L-1 after setup");
+      src = ctx->pmass; bytes = ctx->Vp * sizeof(double); break;
+    default: return ctx->fail(AGCA_EINVAL, "unknown field");
+  }
+  if (bytes) CK(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return AGCA_OK;
+}
+
+}  // extern "C"

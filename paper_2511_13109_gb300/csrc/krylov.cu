@@ -1,0 +1,332 @@
+// Krylov-side kernels (FP64): deterministic dot products, the preconditioned
+// MINRES recurrence of Remark 6 with its scalars kept on the device, the
+// pressure block of the block-diagonal preconditioner, the load vector and
+// the element sensitivities of the adjoint gradient.
+#include <math.h>
+
+#include "agca_internal.cuh"
+
+namespace agca {
+
+namespace {
+
+constexpr int kRedBlocks = 1216;  // 8 per SM; fixed so reductions are deterministic
+constexpr int kRedThreads = 256;
+
+struct DotPairs {
+  const double* x[3];
+  const double* y[3];
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kRedThreads) dot_partial_kernel(DotPairs p, int64_t n, double* partials) {
+  double acc[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) acc[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc[j] = fma(p.x[j][i], p.y[j][i], acc[j]);
+  }
+  __shared__ double red[NP][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    double v = acc[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[j][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NP) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
+    partials[threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// one block: out[j] = scale * sum_b partials[j*nb + b], fixed tree order
+__global__ void reduce_final_kernel(const double* partials, int nb, int np, double* out, double scale) {
+  __shared__ double red[256];
+  for (int j = 0; j < np; ++j) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[j * nb + b];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = scale * red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void sum_partial_kernel(const double* x, int64_t n, double* partials) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += x[i];
+  __shared__ double red[kRedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w];
+    partials[blockIdx.x] = v;
+  }
+}
+
+// ------------------------------------------------------------------ MINRES
+// Scalars live in device memory (MinresSlot) so an iteration needs no host
+// round trip; the Lanczos vector z is kept unnormalized (z = gamma zhat).
+__global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const double* __restrict__ v,
+                               double* vold_to_vnew, const double* __restrict__ sc) {
+  if (sc[MS_DONE] != 0.0) return;
+  const double g = sc[MS_GAMMA], go = sc[MS_GAMMA_OLD];
+  const double ig = 1.0 / g;
+  const double delta = sc[MS_DOT_KZZ] * ig * ig;  // z is kept unnormalized: z = gamma * zhat
+  const double a = delta * ig, b = g / go;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vold_to_vnew[i] = kz[i] * ig - a * v[i] - b * vold_to_vnew[i];
+}
+
+__global__ void minres_scalar_kernel(double* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc[MS_DONE] != 0.0) return;
+  const double g = sc[MS_GAMMA];
+  const double delta = sc[MS_DOT_KZZ] / (g * g);
+  const double gn2 = sc[MS_DOT_ZV];
+  const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
+  const double c = sc[MS_C], co = sc[MS_C_OLD], s = sc[MS_S], so = sc[MS_S_OLD];
+  const double a0 = c * delta - co * s * g;
+  const double a1 = sqrt(a0 * a0 + gn * gn);
+  const double a2 = s * delta + co * c * g;
+  const double a3 = so * g;
+  const double eta = sc[MS_ETA];
+  if (!(a1 > 0.0) || !isfinite(a1)) {  // exact convergence or breakdown
+    sc[MS_DONE] = 2.0;
+    sc[MS_UPD_SKIP] = 1.0;
+    return;
+  }
+  const double cn = a0 / a1, sn = gn / a1;
+  sc[MS_A1] = a1;
+  sc[MS_A2] = a2;
+  sc[MS_A3] = a3;
+  sc[MS_XCOEF] = cn * eta;
+  sc[MS_INV_GAMMA_PREV] = 1.0 / g;
+  sc[MS_UPD_SKIP] = 0.0;
+  sc[MS_ETA] = -sn * eta;
+  sc[MS_C_OLD] = c;
+  sc[MS_C] = cn;
+  sc[MS_S_OLD] = s;
+  sc[MS_S] = sn;
+  sc[MS_GAMMA_OLD] = g;
+  sc[MS_GAMMA] = gn;
+  sc[MS_ITERS] += 1.0;
+  if (fabs(sc[MS_ETA]) <= sc[MS_TOL_ABS] || !(gn > 0.0)) sc[MS_DONE] = 1.0;
+}
+
+// w_new = (z/gamma_prev - a3 w_old - a2 w) / a1 into w_old; x += c_new*eta_prev * w_new
+__global__ void minres_update_kernel(int64_t n, const double* __restrict__ z, const double* __restrict__ w,
+                                     double* wold_to_wnew, double* x, const double* __restrict__ sc) {
+  if (sc[MS_UPD_SKIP] != 0.0) return;
+  const double ig = sc[MS_INV_GAMMA_PREV], a1 = sc[MS_A1], a2 = sc[MS_A2], a3 = sc[MS_A3], xc = sc[MS_XCOEF];
+  const double ia1 = 1.0 / a1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (z[i] * ig - a3 * wold_to_wnew[i] - a2 * w[i]) * ia1;
+    wold_to_wnew[i] = wn;
+    x[i] = fma(xc, wn, x[i]);
+  }
+}
+
+__global__ void minres_init_kernel(double* sc, double tol_rel) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double g2 = sc[MS_DOT_ZV];
+  const double g = g2 > 0.0 ? sqrt(g2) : 0.0;
+  sc[MS_GAMMA] = g;
+  sc[MS_GAMMA_OLD] = 1.0;
+  sc[MS_ETA] = g;
+  sc[MS_ETA0] = g;
+  sc[MS_C] = sc[MS_C_OLD] = 1.0;
+  sc[MS_S] = sc[MS_S_OLD] = 0.0;
+  sc[MS_ITERS] = 0.0;
+  sc[MS_UPD_SKIP] = 1.0;
+  sc[MS_TOL_ABS] = tol_rel * g;
+  sc[MS_DONE] = (g > 0.0) ? 0.0 : 1.0;
+}
+
+// ------------------------------------------------------------------ vectors
+__global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
+                              const double* scal) {
+  const double s0 = scal ? scal[0] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    switch (op) {
+      case VOP_SUB: y[i] = a[i] - b[i]; break;            // y = a - b
+      case VOP_ADD: y[i] = a[i] + b[i]; break;            // y = a + b
+      case VOP_COPY: y[i] = a[i]; break;                  // y = a
+      case VOP_ZERO: y[i] = 0.0; break;                   // y = 0
+      case VOP_PDIV: y[i] = (a[i] - s0) * b[i]; break;    // y = (a - mean) * minv
+      case VOP_SUBS: y[i] = a[i] - s0; break;             // y = a - s
+      case VOP_MUL: y[i] = a[i] * b[i]; break;            // y = a * b
+      case VOP_SCALE_RSQRT: y[i] = a[i] * (1.0 / sqrt(s0)); break;  // y = a / sqrt(s)
+      default: break;
+    }
+  }
+}
+
+// --------------------------------------------------------------- FE kernels
+__global__ void load_vector_kernel(int n, const double* __restrict__ fbar, double* __restrict__ b) {
+  const int nv = n + 1;
+  const int64_t V = nverts(n), E = nelems(n);
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
+  const double w = 1.0 / (24.0 * (double)n * n * n);  // |T| / 4
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (inner) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int64_t cube = (i - (o & 1)) + (int64_t)n * ((j - ((o >> 1) & 1)) + (int64_t)n * (k - ((o >> 2) & 1)));
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        if (corner_local(t, o) < 0) continue;
+        const int64_t e = 6 * cube + t;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += w * fbar[c * E + e];
+      }
+    }
+  }
+  for (int c = 0; c < 3; ++c) b[c * V + v] = acc[c];
+}
+
+// g_e = -eta_e (h/12) S(u) : S(lambda), S(w) = Gw + Gw^T the doubled symmetric
+// gradient scaled by h (this is -lambda_e^T (eta_e dA_e/deta_e) u_e).
+__global__ void sensitivity_kernel(int n, const double* __restrict__ eta, const double* __restrict__ lam,
+                                   const double* __restrict__ u, double* __restrict__ g) {
+  const int nv = n + 1;
+  const int64_t V = nverts(n);
+  const int64_t cube = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (cube >= (int64_t)n * n * n) return;
+  const int ci = (int)(cube % n), cj = (int)((cube / n) % n), ck = (int)(cube / ((int64_t)n * n));
+  double U[8][3], Lm[8][3];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = ci + (q & 1), j = cj + ((q >> 1) & 1), k = ck + ((q >> 2) & 1);
+    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
+    const int64_t v = i + (int64_t)nv * (j + (int64_t)nv * k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      U[q][c] = inner ? u[c * V + v] : 0.0;
+      Lm[q][c] = inner ? lam[c * V + v] : 0.0;
+    }
+  }
+  const double h12 = 1.0 / (12.0 * n);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    double Gu[3][3], Gl[3][3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      const int qa = tet_corner(t, kk), qb = tet_corner(t, kk + 1), m = perm(t, kk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Gu[c][m] = U[qb][c] - U[qa][c];
+        Gl[c][m] = Lm[qb][c] - Lm[qa][c];
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc += (Gu[a][b] + Gu[b][a]) * (Gl[a][b] + Gl[b][a]);
+    const int64_t e = 6 * cube + t;
+    g[e] = -eta[e] * h12 * acc;
+  }
+}
+
+__global__ void mask_boundary_kernel(int n, double* x) {
+  const int nv = n + 1;
+  const int64_t V = nverts(n);
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < 3 * V; id += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = id % V;
+    const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+    if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) x[id] = 0.0;
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s) {
+  mask_boundary_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x);
+  return cudaGetLastError();
+}
+
+int dot_blocks() { return kRedBlocks; }
+
+cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
+                        double* out, double scale, cudaStream_t s) {
+  DotPairs p{};
+  for (int j = 0; j < npairs; ++j) {
+    p.x[j] = xs[j];
+    p.y[j] = ys[j];
+  }
+  switch (npairs) {
+    case 1: dot_partial_kernel<1><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
+    case 2: dot_partial_kernel<2><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
+    case 3: dot_partial_kernel<3><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  reduce_final_kernel<<<1, 256, 0, s>>>(partials, kRedBlocks, npairs, out, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s) {
+  sum_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
+  reduce_final_kernel<<<1, 256, 0, s>>>(partials, kRedBlocks, 1, out, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
+                          const double* scal, cudaStream_t s) {
+  vec_op_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(op, n, y, a, b, c, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s) {
+  minres_init_kernel<<<1, 32, 0, s>>>(sc, tol_rel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, const double* sc,
+                           cudaStream_t s) {
+  lanczos_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, kz, v, vold_to_vnew, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minres_scalars(double* sc, cudaStream_t s) {
+  minres_scalar_kernel<<<1, 32, 0, s>>>(sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minres_update(int64_t n, const double* z, const double* w, double* wold_to_wnew, double* x,
+                                 const double* sc, cudaStream_t s) {
+  minres_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, z, w, wold_to_wnew, x, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_vector(int n, const double* fbar, double* b, cudaStream_t s) {
+  load_vector_kernel<<<blocks_for(nverts(n), 128), 128, 0, s>>>(n, fbar, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
+                               cudaStream_t s) {
+  sensitivity_kernel<<<blocks_for((int64_t)n * n * n, 128), 128, 0, s>>>(n, eta, lam, u, g);
+  return cudaGetLastError();
+}
+
+}  // namespace agca

@@ -1,0 +1,217 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: FP64 operator applies, Galerkin matrices and diagonals 1e-12
+relative; viscosity hierarchy, flags and flagged lists bit-exact; FP32
+(mixed) applies 1e-5 relative (a sum of about 100 FP32 products per output);
+V-cycles 1e-9 (the exact coarsest solve multiplies rounding by the coarsest
+condition number); solutions 1e-8.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import agca as oagca
+from oracle import stokes as ostokes
+from oracle.mesh import Mesh
+from synth import cube_sinker, random_vector, sphere_sinkers
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2511_13109_gb300")
+DEV = torch.device("cuda:0")
+
+
+def _rand_eta(N, seed, lo=-3.0, hi=3.0):
+    m = 6 * (2 * N) ** 3
+    return np.exp(np.random.default_rng(seed).uniform(lo, hi, m) * np.log(10.0))
+
+
+CASES = {
+    # name: (N, L, eta, fbar, nu)
+    "cube16": lambda: (16, 4, cube_sinker(16).eta, cube_sinker(16).fbar, 10.0),
+    "spheres8": lambda: (8, 3, *(lambda p: (p.eta, p.fbar))(sphere_sinkers(8, 3, 0.15, 0.02, 1e6)), 10.0),
+    "random4": lambda: (4, 2, _rand_eta(4, 1), cube_sinker(4).fbar, 10.0),
+    "allflag4": lambda: (4, 3, _rand_eta(4, 2, -1, 1), cube_sinker(4).fbar, 0.5),
+    "noflag6": lambda: (6, 2, _rand_eta(6, 3, -0.2, 0.2), cube_sinker(6).fbar, 1e9),
+}
+
+
+class Case:
+    def __init__(self, name):
+        self.name = name
+        self.N, self.L, self.eta, self.fbar, self.nu = CASES[name]()
+        self.H = oagca.Hierarchy(self.N, self.L, self.eta, self.nu)
+        self.S = ostokes.Stokes(self.H)
+        self.ctx = pkg.Context(self.N, self.L, pkg.FP64, device=DEV)
+        self.ctx.prepare(torch.from_numpy(self.eta).to(DEV), self.nu)
+        self.mctx = pkg.Context(self.N, self.L, pkg.MIXED, device=DEV)
+        self.mctx.prepare(torch.from_numpy(self.eta).to(DEV), self.nu)
+
+
+_cache = {}
+
+
+@pytest.fixture(params=list(CASES))
+def case(request):
+    if request.param not in _cache:
+        _cache[request.param] = Case(request.param)
+    return _cache[request.param]
+
+
+def _d(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _h(t):
+    return t.detach().cpu().numpy()
+
+
+def test_hierarchy_and_flags_bit_exact(case):
+    for l in range(1, case.L):
+        for field, ref in ((pkg.FIELD_MEAN, case.H.mean[l]), (pkg.FIELD_MAX, case.H.mx[l]),
+                           (pkg.FIELD_MIN, case.H.mn[l])):
+            got = _h(case.ctx.level_data(l, field))
+            assert np.array_equal(got, ref), (l, field)
+        flags = _h(case.ctx.level_data(l, pkg.FIELD_FLAGS)).astype(bool)
+        assert np.array_equal(flags, case.H.flags[l])
+        lst = _h(case.ctx.level_data(l, pkg.FIELD_LIST))
+        assert np.array_equal(lst, case.H.flist[l])
+        assert case.ctx.level_info(l).n_flag == len(case.H.flist[l])
+    if case.name == "cube16":
+        assert [case.ctx.level_info(l).n_flag for l in (1, 2, 3)] == [24, 0, 0]
+
+
+def test_galerkin_matrices(case):
+    for l in range(1, case.L):
+        nf = len(case.H.flist[l])
+        if nf == 0:
+            continue
+        got = _h(case.ctx.level_data(l, pkg.FIELD_GCA)).reshape(nf, 12, 12)
+        ref = case.H.gca[l]
+        scale = np.abs(ref).reshape(nf, -1).max(axis=1)
+        err = (np.abs(got - ref).reshape(nf, -1).max(axis=1) / scale).max()
+        assert err < 1e-12, (l, err)
+
+
+def test_diagonals(case):
+    for l in range(1, case.L + 1):
+        got = _h(case.ctx.level_data(l, pkg.FIELD_DIAG))
+        ref = case.H.D[l]
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), l
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_level_apply_fp64(case, seed):
+    for l in range(1, case.L + 1):
+        n = 3 * case.ctx.V[l]
+        x = random_vector(n, seed + 10 * l)
+        got = _h(case.ctx.apply(l, _d(x)))
+        ref = case.H.A[l] @ (x * case.H.mask[l])
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), l
+        # boundary outputs are zero
+        assert np.abs(got * (1 - case.H.mask[l])).max() == 0.0
+
+
+def test_level_apply_fp32(case):
+    for l in range(1, case.L + 1):
+        n = 3 * case.mctx.V[l]
+        x = random_vector(n, 5 + l)
+        got = _h(case.mctx.apply(l, _d(x.astype(np.float32)), dtype=pkg.F32)).astype(np.float64)
+        ref = case.H.A[l] @ (x.astype(np.float32).astype(np.float64) * case.H.mask[l])
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), l
+
+
+def test_transfers(case):
+    for l in range(2, case.L + 1):
+        rf = random_vector(3 * case.ctx.V[l], 3 + l) * case.H.mask[l]
+        got = _h(case.ctx.restrict(l, _d(rf)))
+        ref = case.H.P[l - 1].T @ rf
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+        ec = random_vector(3 * case.ctx.V[l - 1], 9 + l) * case.H.mask[l - 1]
+        xf = random_vector(3 * case.ctx.V[l], 11 + l) * case.H.mask[l]
+        got = _h(case.ctx.prolong_add(l, _d(ec), _d(xf)))
+        ref = xf + case.H.P[l - 1] @ ec
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_lambda_and_coarsest(case):
+    for l in range(2, case.L + 1):
+        lam = case.ctx.level_info(l).lambda_
+        assert abs(lam - case.H.lam[l]) <= 1e-10 * case.H.lam[l], (l, lam, case.H.lam[l])
+    m = len(case.H.coarse_idx)
+    got = _h(case.ctx.level_data(1, pkg.FIELD_COARSE)).reshape(m, m)
+    ref = case.H.coarse_dense
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_vcycle(case):
+    n = 3 * case.ctx.V[case.L]
+    r = random_vector(n, 21) * case.H.mask[case.L]
+    ref = case.H.vcycle(r)
+    got = _h(case.ctx.vcycle(_d(r)))
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    gm = _h(case.mctx.vcycle(_d(r)))
+    assert np.abs(gm - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_stokes_pieces(case):
+    nt = case.ctx.nt
+    x = random_vector(nt, 31)
+    x[:case.S.nu_] *= case.S.mask
+    got = _h(case.ctx.stokes_apply(_d(x)))
+    ref = case.S.K(x)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = _h(case.ctx.load_vector(_d(case.fbar.ravel())))
+    bref = case.S.rhs(case.fbar)
+    assert np.abs(b - bref).max() <= 1e-14 * max(np.abs(bref).max(), 1e-300)
+    pm = _h(case.ctx.level_data(case.L - 1, pkg.FIELD_PMASS))
+    assert np.abs(pm - case.S.Mp).max() <= 1e-13 * case.S.Mp.max()
+    r = random_vector(nt, 41)
+    r[:case.S.nu_] *= case.S.mask
+    r[case.S.nu_:] -= r[case.S.nu_:].mean()
+    zg = _h(case.ctx.precondition(_d(r)))
+    zr = case.S.precondition(r)
+    assert np.abs(zg - zr).max() <= 1e-9 * np.abs(zr).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_matches_direct(case, prec):
+    ctx = case.ctx if prec == "fp64" else case.mctx
+    b = ctx.load_vector(_d(case.fbar.ravel()))
+    x, its, rel = ctx.solve(b, 1e-11, 20000)
+    assert rel <= 1e-11
+    if case.N <= 8:
+        xd = case.S.direct(_h(b))
+    else:  # sparse LU is too slow here; the oracle's MINRES is pinned to it at small sizes
+        xd = _reference_solution(case, _h(b))
+    xg = _h(x)
+    assert np.linalg.norm(xg - xd) <= 1e-8 * np.linalg.norm(xd), (its, rel)
+    # true residual recomputed by the oracle
+    bb = _h(b)
+    assert np.linalg.norm(bb - case.S.K(xg)) <= 1.5e-11 * np.linalg.norm(bb)
+
+
+_ref_solutions = {}
+
+
+def _reference_solution(case, b):
+    if case.name not in _ref_solutions:
+        _ref_solutions[case.name] = case.S.solve(b, 1e-13, 1e-14)[0]
+    return _ref_solutions[case.name]
+
+
+def test_element_sensitivity(case):
+    n = 3 * case.ctx.V[case.L]
+    lam = random_vector(n, 51) * case.S.mask
+    u = random_vector(n, 52) * case.S.mask
+    got = _h(case.ctx.element_sensitivity(_d(lam), _d(u)))
+    ref = -case.S.element_sensitivity(lam, u)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_determinism(case):
+    n = 3 * case.ctx.V[case.L]
+    r = _d(random_vector(n, 61) * case.H.mask[case.L])
+    a = case.ctx.vcycle(r).clone()
+    b = case.ctx.vcycle(r).clone()
+    assert torch.equal(a, b)
