@@ -174,6 +174,17 @@ agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, con
 agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const double* dJdu_dev,
                                   double* g_dev, double rtol, int maxit, int* iters);
 
+/* Number of CUDA kernels this context has launched so far (host counter). */
+agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
+/* Per-launch timing of the finest-level stencil kernels (the dominant
+ * kernels of the V-cycle), with CUDA events on the context stream.
+ * enable = 1 starts recording (up to 65536 launches); enable = 0 stops,
+ * synchronizes and returns the summed kernel time in *ms, their compulsory
+ * HBM bytes (element coefficients and vectors read/written once) in *bytes
+ * and the number of timed launches.  Output pointers are host pointers and
+ * may be NULL when enabling. */
+agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, int64_t* launches);
+
 /* Level metadata (host struct).  Synchronizes. */
 agca_status agca_level_info(agca_ctx* ctx, int level, agca_level_info_t* out);
 /* Copy a level field (agca_field) into caller device memory. */

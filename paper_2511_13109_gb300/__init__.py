@@ -25,3 +25,4 @@ from .agca import (  # noqa: F401
     exported_symbols,
     lib,
 )
+from .adjoint import StokesProblem, stokes_velocity  # noqa: F401,E402

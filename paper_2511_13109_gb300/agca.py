@@ -62,6 +62,8 @@ _SIGS = {
     "agca_solve": ([_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "agca_element_sensitivity": ([_P, _P, _P, _P], _I),
     "agca_adjoint_gradient": ([_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I)], _I),
+    "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
+    "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_level_info": ([_P, _I, ctypes.POINTER(LevelInfo)], _I),
     "agca_get_level_data": ([_P, _I, _I, _P], _I),
 }
@@ -248,6 +250,19 @@ class Context:
         return g, its.value
 
     # ---- introspection ---------------------------------------------------------
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(lib().agca_launch_count(self._h, ctypes.byref(n)), "launch_count")
+        return n.value
+
+    def profile_fine(self, enable: bool):
+        """enable=True starts per-launch timing of the finest-level stencil
+        kernels; enable=False stops and returns (ms, bytes, launches)."""
+        ms, by, n = _D(), _D(), ctypes.c_int64()
+        self._check(lib().agca_profile_fine(self._h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(by),
+                                            ctypes.byref(n)), "profile_fine")
+        return ms.value, by.value, n.value
+
     def level_info(self, level: int) -> LevelInfo:
         info = LevelInfo()
         self._check(lib().agca_level_info(self._h, level, ctypes.byref(info)), "level_info")

@@ -77,6 +77,18 @@ struct agca_ctx {
   double nu = 10.0;
   bool have_eta = false, flagged = false, setup_done = false;
   std::string err;
+  // kernel launches issued by this context, and optional per-launch timing
+  // of the finest-level stencil kernels (agca_profile_fine)
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double prof_bytes = 0.0;
+  int64_t prof_launches = 0;
+
+  ~agca_ctx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 
   agca_status fail(agca_status s, const std::string& msg) {
     err = msg;
@@ -90,6 +102,11 @@ struct agca_ctx {
     cudaError_t e_ = (__VA_ARGS__);                                                                  \
     if (e_ != cudaSuccess)                                                                           \
       return ctx->fail(AGCA_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+#define LK(count, ...)          \
+  do {                          \
+    CK(__VA_ARGS__);            \
+    ctx->launches += (count);   \
   } while (0)
 #define CKS(expr)                  \
   do {                             \
@@ -237,6 +254,21 @@ Cheb cheb_params(const agca_ctx* ctx, int l) {
   return c;
 }
 
+// Compulsory HBM bytes per vertex of one finest-level stencil launch: the
+// element coefficients (6 per vertex) plus every vector read and written
+// once (3 components each).
+double stencil_bytes(int mode, size_t s) {
+  const double coef = 6.0 * s, vec = 3.0 * s;
+  switch (mode) {
+    case ST_APPLY: return coef + 2 * vec;        // x in, y out
+    case ST_RESID: return coef + 3 * vec;        // x, b in, r out
+    case ST_CHEB_FIRST: return coef + 4 * vec;   // x, b, D^-1 in, x' out
+    case ST_CHEB_STEP: return coef + 5 * vec;    // x, x_prev, b, D^-1 in, x' out
+    case ST_CHEB_PRE: return coef + 3 * vec;     // b, D^-1 in, x' out
+    default: return 0.0;
+  }
+}
+
 template <typename T>
 agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, const T* xprev, T* out, double s0,
                     double s1, double s2) {
@@ -250,7 +282,15 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
   a.s0 = (T)s0;
   a.s1 = (T)s1;
   a.s2 = (T)s2;
-  CK(launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
+  const bool timed = ctx->prof && l == ctx->L && ctx->ev_used + 2 <= ctx->ev.size();
+  if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+  LK(1, launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
+  if (timed) {
+    CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
+    ctx->ev_used += 2;
+    ctx->prof_bytes += stencil_bytes(mode, sizeof(T)) * (double)lv.V;
+    ctx->prof_launches += 1;
+  }
   return AGCA_OK;
 }
 
@@ -287,7 +327,7 @@ agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur,
 template <typename T>
 agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
   if (l == 1) {
-    CK(launch_coarse_solve<T>(ctx->lev[1].n, ctx->linv_cm, ctx->linv_rm, b, X, ctx->stream));
+    LK(1, launch_coarse_solve<T>(ctx->lev[1].n, ctx->linv_cm, ctx->linv_rm, b, X, ctx->stream));
     *res = X;
     return AGCA_OK;
   }
@@ -299,10 +339,10 @@ agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
   T* r = static_cast<T*>(lv.vr);
   CKS(stencil<T>(ctx, ST_RESID, l, cur, b, nullptr, r, 0, 0, 0));
   T* bc = static_cast<T*>(lc.vb);
-  CK(launch_restrict<T>(lv.n, 3, true, T(1), r, bc, ctx->stream));
+  LK(1, launch_restrict<T>(lv.n, 3, true, T(1), r, bc, ctx->stream));
   T* ec = nullptr;
   CKS(cycle<T>(ctx, l - 1, bc, static_cast<T*>(lc.vx), static_cast<T*>(lc.vt), &ec));
-  CK(launch_prolong<T>(lv.n, 3, true, true, ec, cur, ctx->stream));
+  LK(1, launch_prolong<T>(lv.n, 3, true, true, ec, cur, ctx->stream));
   CKS(chebyshev<T>(ctx, l, b, false, &cur, &other));
   *res = cur;
   return AGCA_OK;
@@ -318,10 +358,10 @@ agca_status vcycle_impl(agca_ctx* ctx, const double* r, double* z) {
     if (res != z) CK(cudaMemcpyAsync(z, res, n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   } else {
     float* b32 = static_cast<float*>(lf.vb);
-    CK(launch_d2f(r, b32, n3, ctx->stream));
+    LK(1, launch_d2f(r, b32, n3, ctx->stream));
     float* res = nullptr;
     CKS(cycle<float>(ctx, L, b32, static_cast<float*>(lf.vx), static_cast<float*>(lf.vt), &res));
-    CK(launch_f2d(res, z, n3, ctx->stream));
+    LK(1, launch_f2d(res, z, n3, ctx->stream));
   }
   return AGCA_OK;
 }
@@ -332,14 +372,14 @@ agca_status stokes_impl(agca_ctx* ctx, const double* x, double* y) {
   const int L = ctx->L;
   const Level& lf = ctx->lev[L];
   const int64_t n3 = 3 * lf.V;
-  CK(launch_prolong<double>(lf.n, 1, false, false, x + n3, ctx->qfine, ctx->stream));
+  LK(1, launch_prolong<double>(lf.n, 1, false, false, x + n3, ctx->qfine, ctx->stream));
   StencilArgs<double> a{};
   a.x = x;
   a.q = ctx->qfine;
   a.out = y;
   a.out2 = ctx->sfine;
-  CK(launch_stencil<double, TC>(ST_STOKES, level_op<TC>(ctx, L), a, ctx->stream));
-  CK(launch_restrict<double>(lf.n, 1, false, -1.0, ctx->sfine, y + n3, ctx->stream));
+  LK(1, launch_stencil<double, TC>(ST_STOKES, level_op<TC>(ctx, L), a, ctx->stream));
+  LK(1, launch_restrict<double>(lf.n, 1, false, -1.0, ctx->sfine, y + n3, ctx->stream));
   return AGCA_OK;
 }
 
@@ -354,17 +394,17 @@ agca_status precond_impl(agca_ctx* ctx, const double* r, double* z) {
   const double* rp = r + n3;
   double* zp = z + n3;
   const double inv = 1.0 / (double)ctx->Vp;
-  CK(launch_sum(rp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP0, inv, ctx->stream));
-  CK(launch_vec_op(VOP_PDIV, ctx->Vp, zp, rp, ctx->pmass_inv, nullptr, ctx->sc + MS_TMP0, ctx->stream));
-  CK(launch_sum(zp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP1, inv, ctx->stream));
-  CK(launch_vec_op(VOP_SUBS, ctx->Vp, zp, zp, nullptr, nullptr, ctx->sc + MS_TMP1, ctx->stream));
+  LK(2, launch_sum(rp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP0, inv, ctx->stream));
+  LK(1, launch_vec_op(VOP_PDIV, ctx->Vp, zp, rp, ctx->pmass_inv, nullptr, ctx->sc + MS_TMP0, ctx->stream));
+  LK(2, launch_sum(zp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP1, inv, ctx->stream));
+  LK(1, launch_vec_op(VOP_SUBS, ctx->Vp, zp, zp, nullptr, nullptr, ctx->sc + MS_TMP1, ctx->stream));
   return AGCA_OK;
 }
 
 agca_status dot1(agca_ctx* ctx, const double* x, const double* y, int64_t n, double* out_dev) {
   const double* xs[1] = {x};
   const double* ys[1] = {y};
-  CK(launch_dots(1, xs, ys, n, ctx->partials, out_dev, 1.0, ctx->stream));
+  LK(2, launch_dots(1, xs, ys, n, ctx->partials, out_dev, 1.0, ctx->stream));
   return AGCA_OK;
 }
 
@@ -388,24 +428,24 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
   double* wold = ctx->kv[KV_WOLD];
   double* w = ctx->kv[KV_W];
   double* kz = ctx->kv[KV_KZ];
-  CK(launch_vec_op(VOP_ZERO, nt, d, nullptr, nullptr, nullptr, nullptr, s));
-  CK(launch_vec_op(VOP_ZERO, nt, vold, nullptr, nullptr, nullptr, nullptr, s));
-  CK(launch_vec_op(VOP_ZERO, nt, wold, nullptr, nullptr, nullptr, nullptr, s));
-  CK(launch_vec_op(VOP_ZERO, nt, w, nullptr, nullptr, nullptr, nullptr, s));
-  CK(launch_vec_op(VOP_COPY, nt, v, b, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, d, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, vold, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, wold, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, w, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_COPY, nt, v, b, nullptr, nullptr, nullptr, s));
   CKS(precond_impl(ctx, v, z));
   CKS(dot1(ctx, z, v, nt, ctx->sc + MS_DOT_ZV));
-  CK(launch_minres_init(ctx->sc, tol_rel, s));
+  LK(1, launch_minres_init(ctx->sc, tol_rel, s));
   const int check_every = 4;
   int it = 0;
   for (; it < maxit; ++it) {
     CKS(stokes_dispatch(ctx, z, kz, low));
     CKS(dot1(ctx, kz, z, nt, ctx->sc + MS_DOT_KZZ));
-    CK(launch_lanczos(nt, kz, v, vold, ctx->sc, s));  // vold <- v_new
+    LK(1, launch_lanczos(nt, kz, v, vold, ctx->sc, s));  // vold <- v_new
     CKS(precond_impl(ctx, vold, zn));
     CKS(dot1(ctx, zn, vold, nt, ctx->sc + MS_DOT_ZV));
-    CK(launch_minres_scalars(ctx->sc, s));
-    CK(launch_minres_update(nt, z, w, wold, d, ctx->sc, s));  // wold <- w_new
+    LK(1, launch_minres_scalars(ctx->sc, s));
+    LK(1, launch_minres_update(nt, z, w, wold, d, ctx->sc, s));  // wold <- w_new
     std::swap(vold, v);
     std::swap(z, zn);
     std::swap(wold, w);
@@ -423,8 +463,8 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
 
 agca_status project_pressure(agca_ctx* ctx, double* x) {
   const int64_t n3 = 3 * ctx->lev[ctx->L].V;
-  CK(launch_sum(x + n3, ctx->Vp, ctx->partials, ctx->sc + MS_TMP2, 1.0 / (double)ctx->Vp, ctx->stream));
-  CK(launch_vec_op(VOP_SUBS, ctx->Vp, x + n3, x + n3, nullptr, nullptr, ctx->sc + MS_TMP2, ctx->stream));
+  LK(2, launch_sum(x + n3, ctx->Vp, ctx->partials, ctx->sc + MS_TMP2, 1.0 / (double)ctx->Vp, ctx->stream));
+  LK(1, launch_vec_op(VOP_SUBS, ctx->Vp, x + n3, x + n3, nullptr, nullptr, ctx->sc + MS_TMP2, ctx->stream));
   return AGCA_OK;
 }
 
@@ -437,10 +477,10 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
   double* kx = ctx->kv[KV_KZ];
   // Dirichlet rows carry no equation: work on a copy of b with them zeroed
   double* bm = ctx->kv[KV_B];
-  CK(launch_vec_op(VOP_COPY, nt, bm, b_in, nullptr, nullptr, nullptr, s));
-  CK(launch_mask_boundary(ctx->lev[ctx->L].n, bm, s));
+  LK(1, launch_vec_op(VOP_COPY, nt, bm, b_in, nullptr, nullptr, nullptr, s));
+  LK(1, launch_mask_boundary(ctx->lev[ctx->L].n, bm, s));
   const double* b = bm;
-  CK(launch_vec_op(VOP_ZERO, nt, x, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, x, nullptr, nullptr, nullptr, nullptr, s));
   double nb2 = 0.0;
   CKS(dot1(ctx, b, b, nt, ctx->sc + MS_TMP0));
   CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nb2));
@@ -450,7 +490,7 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
   const bool mixed = ctx->prec == AGCA_MIXED;
   for (int outer = 0; outer < 60 && nb > 0.0; ++outer) {
     CKS(stokes_dispatch(ctx, x, kx, false));
-    CK(launch_vec_op(VOP_SUB, nt, r, b, kx, nullptr, nullptr, s));
+    LK(1, launch_vec_op(VOP_SUB, nt, r, b, kx, nullptr, nullptr, s));
     double nr2 = 0.0;
     CKS(dot1(ctx, r, r, nt, ctx->sc + MS_TMP0));
     CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nr2));
@@ -462,7 +502,7 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
     int its = 0;
     CKS(minres_impl(ctx, r, d, inner, maxit - total, mixed, &its));
     total += its;
-    CK(launch_vec_op(VOP_ADD, nt, x, x, d, nullptr, nullptr, s));
+    LK(1, launch_vec_op(VOP_ADD, nt, x, x, d, nullptr, nullptr, s));
     CKS(project_pressure(ctx, x));
     if (its == 0) break;
   }
@@ -487,16 +527,16 @@ agca_status power_lambda(agca_ctx* ctx, int l, double* lam) {
   cudaStream_t s = ctx->stream;
   double* v = ctx->kv[KV_VOLD];
   double* w = ctx->kv[KV_V];
-  CK(launch_start_vector(lv.n, v, s));
+  LK(1, launch_start_vector(lv.n, v, s));
   for (int it = 0; it < ctx->power_iters; ++it) {
     CKS(stencil<double>(ctx, ST_APPLY, l, v, nullptr, nullptr, w, 0, 0, 0));
-    CK(launch_vec_op(VOP_MUL, n3, w, w, lv.invD64, nullptr, nullptr, s));
+    LK(1, launch_vec_op(VOP_MUL, n3, w, w, lv.invD64, nullptr, nullptr, s));
     CKS(dot1(ctx, w, w, n3, ctx->sc + MS_TMP0));
-    CK(launch_vec_op(VOP_SCALE_RSQRT, n3, v, w, nullptr, nullptr, ctx->sc + MS_TMP0, s));
+    LK(1, launch_vec_op(VOP_SCALE_RSQRT, n3, v, w, nullptr, nullptr, ctx->sc + MS_TMP0, s));
   }
   CKS(stencil<double>(ctx, ST_APPLY, l, v, nullptr, nullptr, w, 0, 0, 0));
   CKS(dot1(ctx, v, w, n3, ctx->sc + MS_TMP0));
-  CK(launch_vec_op(VOP_MUL, n3, w, v, lv.diag, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_MUL, n3, w, v, lv.diag, nullptr, nullptr, s));
   CKS(dot1(ctx, v, w, n3, ctx->sc + MS_TMP1));
   double num = 0.0, den = 0.0;
   CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &num));
@@ -608,17 +648,17 @@ agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
   cudaStream_t s = ctx->stream;
   const int L = ctx->L;
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), s));
-  CK(launch_check_eta(ctx->lev[L].mean, ctx->lev[L].E, ctx->status, s));
+  LK(1, launch_check_eta(ctx->lev[L].mean, ctx->lev[L].E, ctx->status, s));
   CKS(check_status(ctx, "agca_flag"));
   ctx->nu = nu;
   for (int l = L - 1; l >= 1; --l) {
     Level& lc = ctx->lev[l];
     const Level& lf = ctx->lev[l + 1];
-    CK(launch_coarsen(lc.n, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
+    LK(1, launch_coarsen(lc.n, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
   }
   for (int l = 1; l < L; ++l) {
     Level& lc = ctx->lev[l];
-    CK(launch_compact(lc.flags, lc.E, lc.fidx, lc.list, ctx->block_counts, ctx->totals + l, s));
+    LK(3, launch_compact(lc.flags, lc.E, lc.fidx, lc.list, ctx->block_counts, ctx->totals + l, s));
   }
   std::vector<int64_t> tot(L + 1, 0);
   CK(cudaMemcpyAsync(tot.data(), ctx->totals, (L + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -655,25 +695,25 @@ agca_status agca_setup(agca_ctx* ctx) {
     Level& lc = ctx->lev[l];
     const Level& lf = ctx->lev[l + 1];
     const bool child_finest = (l + 1 == L);
-    CK(launch_galerkin(lc.n, lc.n_flag, lc.list, lf.n, child_finest, lf.mean, child_finest ? nullptr : lf.fidx,
+    LK(1, launch_galerkin(lc.n, lc.n_flag, lc.list, lf.n, child_finest, lf.mean, child_finest ? nullptr : lf.fidx,
                        child_finest ? nullptr : lf.gca64, lc.gca64, s));
   }
   for (int l = 1; l <= L; ++l) {
     Level& lv = ctx->lev[l];
     if (mixed) {
-      CK(launch_d2f(lv.mean, lv.mean32, lv.E, s));
-      if (l < L) CK(launch_gca_to_f32(lv.n_flag, lv.list, lv.mx, lv.gca64, lv.gca32, lv.gscale32, s));
+      LK(1, launch_d2f(lv.mean, lv.mean32, lv.E, s));
+      if (l < L) LK(1, launch_gca_to_f32(lv.n_flag, lv.list, lv.mx, lv.gca64, lv.gca32, lv.gscale32, s));
     }
-    CK(launch_diag(op64(ctx, l), lv.diag, lv.invD64, mixed ? lv.invD32 : nullptr, s));
+    LK(1, launch_diag(op64(ctx, l), lv.diag, lv.invD64, mixed ? lv.invD32 : nullptr, s));
   }
   // coarsest operator: dense assembly, Cholesky, explicit inverse factor
-  CK(launch_coarse_assemble(op64(ctx, 1), ctx->cdense, s));
+  LK(1, launch_coarse_assemble(op64(ctx, 1), ctx->cdense, s));
   CK(cudaMemcpyAsync(ctx->cfac, ctx->cdense, (size_t)ctx->mc * ctx->mc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(launch_cholesky(ctx->cfac, ctx->mc, ctx->status, s));
-  CK(launch_trinv(ctx->cfac, ctx->mc, ctx->linv_cm, ctx->linv_rm, s));
+  LK(1, launch_cholesky(ctx->cfac, ctx->mc, ctx->status, s));
+  LK(1, launch_trinv(ctx->cfac, ctx->mc, ctx->linv_cm, ctx->linv_rm, s));
   CKS(check_status(ctx, "agca_setup"));
   for (int l = 2; l <= L; ++l) CKS(power_lambda(ctx, l, &ctx->lev[l].lambda));
-  CK(launch_pressure_mass(ctx->lev[L].n / 2, ctx->lev[L].mean, ctx->pmass, ctx->pmass_inv, s));
+  LK(1, launch_pressure_mass(ctx->lev[L].n / 2, ctx->lev[L].mean, ctx->pmass, ctx->pmass_inv, s));
   CK(cudaStreamSynchronize(s));
   ctx->setup_done = true;
   return AGCA_OK;
@@ -698,10 +738,10 @@ agca_status agca_restrict(agca_ctx* ctx, int level, int dtype, const void* rf_de
   if (level < 2 || level > ctx->L) return ctx->fail(AGCA_EINVAL, "level out of range");
   const int nf = ctx->lev[level].n;
   if (dtype == AGCA_F64)
-    CK(launch_restrict<double>(nf, 3, true, 1.0, static_cast<const double*>(rf_dev), static_cast<double*>(rc_dev),
+    LK(1, launch_restrict<double>(nf, 3, true, 1.0, static_cast<const double*>(rf_dev), static_cast<double*>(rc_dev),
                                ctx->stream));
   else if (dtype == AGCA_F32)
-    CK(launch_restrict<float>(nf, 3, true, 1.0f, static_cast<const float*>(rf_dev), static_cast<float*>(rc_dev),
+    LK(1, launch_restrict<float>(nf, 3, true, 1.0f, static_cast<const float*>(rf_dev), static_cast<float*>(rc_dev),
                               ctx->stream));
   else
     return ctx->fail(AGCA_EINVAL, "bad dtype");
@@ -713,10 +753,10 @@ agca_status agca_prolong_add(agca_ctx* ctx, int level, int dtype, const void* ec
   if (level < 2 || level > ctx->L) return ctx->fail(AGCA_EINVAL, "level out of range");
   const int nf = ctx->lev[level].n;
   if (dtype == AGCA_F64)
-    CK(launch_prolong<double>(nf, 3, true, true, static_cast<const double*>(ec_dev), static_cast<double*>(xf_dev),
+    LK(1, launch_prolong<double>(nf, 3, true, true, static_cast<const double*>(ec_dev), static_cast<double*>(xf_dev),
                               ctx->stream));
   else if (dtype == AGCA_F32)
-    CK(launch_prolong<float>(nf, 3, true, true, static_cast<const float*>(ec_dev), static_cast<float*>(xf_dev),
+    LK(1, launch_prolong<float>(nf, 3, true, true, static_cast<const float*>(ec_dev), static_cast<float*>(xf_dev),
                              ctx->stream));
   else
     return ctx->fail(AGCA_EINVAL, "bad dtype");
@@ -744,7 +784,7 @@ agca_status agca_precondition(agca_ctx* ctx, const double* r_dev, double* z_dev)
 agca_status agca_load_vector(agca_ctx* ctx, const double* fbar_dev, double* b_dev) {
   if (!ctx || !fbar_dev || !b_dev) return AGCA_EINVAL;
   const Level& lf = ctx->lev[ctx->L];
-  CK(launch_load_vector(lf.n, fbar_dev, b_dev, ctx->stream));
+  LK(1, launch_load_vector(lf.n, fbar_dev, b_dev, ctx->stream));
   CK(cudaMemsetAsync(b_dev + 3 * lf.V, 0, ctx->Vp * sizeof(double), ctx->stream));
   return AGCA_OK;
 }
@@ -761,7 +801,7 @@ agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, con
   if (!ctx || !lam_u_dev || !u_dev || !g_dev) return AGCA_EINVAL;
   if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
   const Level& lf = ctx->lev[ctx->L];
-  CK(launch_sensitivity(lf.n, lf.mean, lam_u_dev, u_dev, g_dev, ctx->stream));
+  LK(1, launch_sensitivity(lf.n, lf.mean, lam_u_dev, u_dev, g_dev, ctx->stream));
   return AGCA_OK;
 }
 
@@ -781,8 +821,44 @@ agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const doub
   const agca_status st = solve_impl(ctx, rhs, lam, rtol, maxit, &its, &rel);
   if (iters) *iters = its;
   if (st != AGCA_OK) return st;
-  CK(launch_sensitivity(lf.n, lf.mean, lam, x_dev, g_dev, ctx->stream));
+  LK(1, launch_sensitivity(lf.n, lf.mean, lam, x_dev, g_dev, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return AGCA_OK;
+}
+
+agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return AGCA_EINVAL;
+  *launches = ctx->launches;
+  return AGCA_OK;
+}
+
+agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, int64_t* launches) {
+  if (!ctx) return AGCA_EINVAL;
+  if (enable) {
+    const size_t want = 2 * 65536;
+    while (ctx->ev.size() < want) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    ctx->ev_used = 0;
+    ctx->prof_bytes = 0.0;
+    ctx->prof_launches = 0;
+    ctx->prof = true;
+    return AGCA_OK;
+  }
+  ctx->prof = false;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (bytes) *bytes = ctx->prof_bytes;
+  if (launches) *launches = ctx->prof_launches;
+  ctx->ev_used = 0;
   return AGCA_OK;
 }
 

@@ -4,7 +4,10 @@ Tolerances: FP64 operator applies, Galerkin matrices and diagonals 1e-12
 relative; viscosity hierarchy, flags and flagged lists bit-exact; FP32
 (mixed) applies 1e-5 relative (a sum of about 100 FP32 products per output);
 V-cycles 1e-9 (the exact coarsest solve multiplies rounding by the coarsest
-condition number); solutions 1e-8.
+condition number); solutions 1e-8 relative to the oracle's solution, with
+both sides solved to a 1e-12 relative residual (the error is the residual
+times the condition number, which for element-wise random 1e6 contrasts
+exceeds 1e3).
 """
 import numpy as np
 import pytest
@@ -178,8 +181,8 @@ def test_stokes_pieces(case):
 def test_solve_matches_direct(case, prec):
     ctx = case.ctx if prec == "fp64" else case.mctx
     b = ctx.load_vector(_d(case.fbar.ravel()))
-    x, its, rel = ctx.solve(b, 1e-11, 20000)
-    assert rel <= 1e-11
+    x, its, rel = ctx.solve(b, 1e-12, 20000)
+    assert rel <= 1e-12
     if case.N <= 8:
         xd = case.S.direct(_h(b))
     else:  # sparse LU is too slow here; the oracle's MINRES is pinned to it at small sizes
@@ -188,7 +191,7 @@ def test_solve_matches_direct(case, prec):
     assert np.linalg.norm(xg - xd) <= 1e-8 * np.linalg.norm(xd), (its, rel)
     # true residual recomputed by the oracle
     bb = _h(b)
-    assert np.linalg.norm(bb - case.S.K(xg)) <= 1.5e-11 * np.linalg.norm(bb)
+    assert np.linalg.norm(bb - case.S.K(xg)) <= 1.5e-12 * np.linalg.norm(bb)
 
 
 _ref_solutions = {}
@@ -196,7 +199,7 @@ _ref_solutions = {}
 
 def _reference_solution(case, b):
     if case.name not in _ref_solutions:
-        _ref_solutions[case.name] = case.S.solve(b, 1e-13, 1e-14)[0]
+        _ref_solutions[case.name] = case.S.solve(b, 1e-12, 1e-13)[0]
     return _ref_solutions[case.name]
 
 
