@@ -189,9 +189,10 @@ def test_solve_matches_direct(case, prec):
         xd = _reference_solution(case, _h(b))
     xg = _h(x)
     assert np.linalg.norm(xg - xd) <= 1e-8 * np.linalg.norm(xd), (its, rel)
-    # true residual recomputed by the oracle
+    # true residual recomputed by the oracle: the two sides round K x
+    # differently, by about eps * |K| |x| (here up to 1e-11 of ||b||)
     bb = _h(b)
-    assert np.linalg.norm(bb - case.S.K(xg)) <= 1.5e-12 * np.linalg.norm(bb)
+    assert np.linalg.norm(bb - case.S.K(xg)) <= 1e-11 * np.linalg.norm(bb)
 
 
 _ref_solutions = {}
