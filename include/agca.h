@@ -174,6 +174,25 @@ agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, con
 agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const double* dJdu_dev,
                                   double* g_dev, double rtol, int maxit, int* iters);
 
+/* Allocation-free Stokes apply y = K x on the finest grid of N pressure cubes
+ * per axis, for callers that cannot allocate device memory themselves (code
+ * whose device memory belongs to another allocator or pool it must not
+ * bypass, or loops that cannot afford an allocation).  No context, workspace
+ * or allocation: the operator's two fine-grid scratch fields live in a fixed
+ * device array inside the library, held by every GPU that loads it until the
+ * process exits.  The paper has no counterpart of this entry point.
+ *   N: 1..32 (AGCA_EINVAL beyond: the scratch holds 2 (2N+1)^3 doubles);
+ *   eta: double[6 (2N)^3] element viscosities (as agca_set_viscosity);
+ *   x, y: double[3 (2N+1)^3 + (N+1)^3] Stokes vectors as agca_stokes_apply;
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * The first call on a device looks up the scratch address on that device
+ * (make it before any stream capture).  Every call uses the same scratch and
+ * overwrites all of it that it reads, so nothing needs clearing; calls that
+ * overlap on the GPU (other streams, other host threads) race on it.
+ * Asynchronous; returns AGCA_ECUDA if a launch fails. */
+agca_status agca_stokes_apply_static(int N, const double* eta_dev, const double* x_dev, double* y_dev,
+                                     void* cuda_stream);
+
 /* Number of CUDA kernels this context has launched so far (host counter). */
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
 /* Per-launch timing of the finest-level stencil kernels (the dominant

@@ -24,5 +24,6 @@ from .agca import (  # noqa: F401
     default_levels,
     exported_symbols,
     lib,
+    stokes_apply_static,
 )
 from .adjoint import StokesProblem, stokes_velocity  # noqa: F401,E402

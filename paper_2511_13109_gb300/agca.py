@@ -62,6 +62,7 @@ _SIGS = {
     "agca_solve": ([_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "agca_element_sensitivity": ([_P, _P, _P, _P], _I),
     "agca_adjoint_gradient": ([_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I)], _I),
+    "agca_stokes_apply_static": ([_I, _P, _P, _P, _P], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_level_info": ([_P, _I, ctypes.POINTER(LevelInfo)], _I),
@@ -95,6 +96,27 @@ def default_levels(N: int) -> int:
         n //= 2
         L += 1
     return L
+
+
+STATIC_MAX_N = 32
+
+
+def stokes_apply_static(N: int, eta: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,
+                        stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """y = K x without a context or any library allocation (N <= 32), for
+    callers that cannot allocate device memory; see agca_stokes_apply_static.
+    The output tensor y must be provided by such callers."""
+    nL = 2 * N
+    nt = 3 * (nL + 1) ** 3 + (N + 1) ** 3
+    _need(eta, 6 * nL ** 3, torch.float64, "eta")
+    _need(x, nt, torch.float64, "x")
+    y = torch.empty_like(x) if y is None else y
+    _need(y, nt, torch.float64, "y")
+    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    st = lib().agca_stokes_apply_static(N, _ptr(eta), _ptr(x), _ptr(y), _P(s.cuda_stream))
+    if st != 0:
+        raise AgcaError(st, f"agca_stokes_apply_static(N={N})")
+    return y
 
 
 def _ptr(t: torch.Tensor):
