@@ -76,6 +76,9 @@ struct LevelOp {
   const int32_t* fidx; // compact Galerkin index per element or -1; nullptr on finest
   const T* gca;        // stored Galerkin matrices (n_flag * 144)
   const T* gscale;     // per flagged element scale (mixed) or nullptr
+  const int32_t* list; // flagged element ids (coarse levels)
+  int64_t n_flag;      // number of flagged elements
+  T* ye;               // n_flag * 12 scratch: s_e A_e x_e of the flagged elements
 };
 
 __host__ __device__ inline int64_t nverts(int n) { return (int64_t)(n + 1) * (n + 1) * (n + 1); }

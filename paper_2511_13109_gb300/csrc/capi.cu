@@ -36,6 +36,9 @@ struct Level {
   float* invD32 = nullptr;
   float* gca32 = nullptr;
   float* gscale32 = nullptr;
+  // s_e A_e x_e of the flagged elements (coarse-apply scratch)
+  double* ye64 = nullptr;
+  float* ye32 = nullptr;
   // V-cycle vectors in the cycle precision: rhs, two iterate buffers, residual
   void* vb = nullptr;
   void* vx = nullptr;
@@ -80,6 +83,15 @@ struct agca_ctx {
   // kernel launches issued by this context, and optional per-launch timing
   // of the finest-level stencil kernels (agca_profile_fine)
   int64_t launches = 0;
+  // V-cycles replayed from CUDA graphs, keyed by their (input, output) pointers
+  struct GraphEntry {
+    const void* r;
+    void* z;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<GraphEntry> graphs;
+  bool use_graphs = true;
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
@@ -88,6 +100,11 @@ struct agca_ctx {
 
   ~agca_ctx() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    clear_graphs();
+  }
+  void clear_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
   }
 
   agca_status fail(agca_status s, const std::string& msg) {
@@ -182,7 +199,9 @@ void carve_gca(agca_ctx* ctx, char* base) {
   for (int l = 1; l < ctx->L; ++l) {
     Level& lv = ctx->lev[l];
     lv.gca64 = cv.take<double>(std::max<int64_t>(1, lv.n_flag * 144));
+    lv.ye64 = cv.take<double>(std::max<int64_t>(1, lv.n_flag * 12));
     if (mixed) {
+      lv.ye32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag * 12));
       lv.gca32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag * 144));
       lv.gscale32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag));
     }
@@ -200,6 +219,9 @@ LevelOp<double> op64(const agca_ctx* ctx, int l) {
   if (l < ctx->L) {
     op.fidx = lv.fidx;
     op.gca = lv.gca64;
+    op.list = lv.list;
+    op.n_flag = lv.n_flag;
+    op.ye = lv.ye64;
   }
   return op;
 }
@@ -215,6 +237,9 @@ LevelOp<float> op32(const agca_ctx* ctx, int l) {
     op.fidx = lv.fidx;
     op.gca = lv.gca32;
     op.gscale = lv.gscale32;
+    op.list = lv.list;
+    op.n_flag = lv.n_flag;
+    op.ye = lv.ye32;
   }
   return op;
 }
@@ -284,7 +309,7 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
   a.s2 = (T)s2;
   const bool timed = ctx->prof && l == ctx->L && ctx->ev_used + 2 <= ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
-  LK(1, launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
+  LK((l < ctx->L && lv.n_flag > 0) ? 2 : 1, launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
     ctx->ev_used += 2;
@@ -348,7 +373,7 @@ agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
   return AGCA_OK;
 }
 
-agca_status vcycle_impl(agca_ctx* ctx, const double* r, double* z) {
+agca_status vcycle_direct(agca_ctx* ctx, const double* r, double* z) {
   const int L = ctx->L;
   Level& lf = ctx->lev[L];
   const int64_t n3 = 3 * lf.V;
@@ -363,6 +388,57 @@ agca_status vcycle_impl(agca_ctx* ctx, const double* r, double* z) {
     CKS(cycle<float>(ctx, L, b32, static_cast<float*>(lf.vx), static_cast<float*>(lf.vt), &res));
     LK(1, launch_f2d(res, z, n3, ctx->stream));
   }
+  return AGCA_OK;
+}
+
+// One V-cycle, replayed from a CUDA graph captured on first use for this
+// (r, z) pair: the cycle is a fixed sequence of ~40 launches whose
+// parameters only change at setup.  Direct launches when the stream is the
+// legacy default stream, is already being captured by the caller, or while
+// per-launch timing is on.
+agca_status vcycle_impl(agca_ctx* ctx, const double* r, double* z) {
+  cudaStream_t s = ctx->stream;
+  bool graph = ctx->use_graphs && !ctx->prof && s != nullptr;
+  if (graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    graph = (cs == cudaStreamCaptureStatusNone);
+  }
+  if (!graph) return vcycle_direct(ctx, r, z);
+  for (auto& g : ctx->graphs) {
+    if (g.r == r && g.z == z) {
+      CK(cudaGraphLaunch(g.exec, s));
+      ctx->launches += g.launches;
+      return AGCA_OK;
+    }
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->use_graphs = false;
+    return vcycle_direct(ctx, r, z);
+  }
+  const int64_t l0 = ctx->launches;
+  const agca_status st = vcycle_direct(ctx, r, z);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(s, &g);
+  const int64_t nl = ctx->launches - l0;
+  ctx->launches = l0;
+  if (st != AGCA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ee != cudaSuccess) return ctx->fail(AGCA_ECUDA, std::string("V-cycle capture: ") + cudaGetErrorString(ee));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return ctx->fail(AGCA_ECUDA, std::string("V-cycle graph: ") + cudaGetErrorString(ie));
+  if (ctx->graphs.size() >= 16) {
+    cudaGraphExecDestroy(ctx->graphs.front().exec);
+    ctx->graphs.erase(ctx->graphs.begin());
+  }
+  ctx->graphs.push_back({r, z, exec, nl});
+  CK(cudaGraphLaunch(exec, s));
+  ctx->launches += nl;
   return AGCA_OK;
 }
 
@@ -586,7 +662,7 @@ agca_status agca_create(int N, int n_levels, int prec, void* cuda_stream, agca_c
   }
   const int n1 = ctx->lev[1].n;
   ctx->mc = 3 * (n1 - 1) * (n1 - 1) * (n1 - 1);
-  if (ctx->mc > 6000) {  // the coarsest dense factor must stay small
+  if (ctx->mc > 3000) {  // the coarsest dense factor must stay small (solve staged in 48 KB of shared memory)
     delete ctx;
     return AGCA_EINVAL;
   }
@@ -603,6 +679,7 @@ const char* agca_last_error(const agca_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, int power_iters) {
   if (!ctx) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (degree < 2 || degree > 8 || !(lo > 0.0) || !(hi > lo) || power_iters < 1 || power_iters > 1000)
     return ctx->fail(AGCA_EINVAL, "smoother parameters out of range");
   ctx->cheb_degree = degree;
@@ -621,6 +698,7 @@ agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes) {
 
 agca_status agca_bind_workspace(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
   if (!ctx) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return ctx->fail(AGCA_EINVAL, "workspace must be 256-byte aligned");
   if (bytes < ctx->ws_need) return ctx->fail(AGCA_ENOMEM, "workspace too small");
   ctx->ws = static_cast<char*>(dev_ptr);
@@ -633,6 +711,7 @@ agca_status agca_bind_workspace(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
 
 agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
   if (!ctx || !eta_dev) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (!ctx->ws) return ctx->fail(AGCA_ESTATE, "bind the workspace first");
   Level& lf = ctx->lev[ctx->L];
   CK(cudaMemcpyAsync(lf.mean, eta_dev, lf.E * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -643,6 +722,7 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
 
 agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
   if (!ctx || !gca_bytes) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
   if (!(nu >= 0.0) || !isfinite(nu)) return ctx->fail(AGCA_EINVAL, "nu must be finite and >= 0");
   cudaStream_t s = ctx->stream;
@@ -674,6 +754,7 @@ agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
 
 agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
   if (!ctx) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (!ctx->flagged) return ctx->fail(AGCA_ESTATE, "flag first");
   if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return ctx->fail(AGCA_EINVAL, "store must be 256-byte aligned");
   if (bytes < ctx->gs_need) return ctx->fail(AGCA_ENOMEM, "Galerkin store too small");
@@ -685,6 +766,7 @@ agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
 
 agca_status agca_setup(agca_ctx* ctx) {
   if (!ctx) return AGCA_EINVAL;
+  ctx->clear_graphs();
   if (!ctx->flagged || !ctx->gs) return ctx->fail(AGCA_ESTATE, "flag and bind the Galerkin store first");
   cudaStream_t s = ctx->stream;
   const int L = ctx->L;

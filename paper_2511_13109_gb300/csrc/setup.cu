@@ -317,7 +317,9 @@ __global__ void trinv_kernel(const double* l, int m, double* xcm, double* xrm) {
   }
 }
 
-// z = L^-T L^-1 r on the interior DoFs of level 1, one block; r, z full-grid
+// z = L^-T L^-1 r on the interior DoFs of level 1, one block; r, z full-grid.
+// One warp per row of each triangular product with coalesced row reads
+// (X row-major for t = X r, X column-major for z = X^T t).
 template <typename T>
 __global__ void coarse_solve_kernel(int n, const double* __restrict__ xcm, const double* __restrict__ xrm,
                                     const T* __restrict__ r, T* __restrict__ z) {
@@ -327,22 +329,27 @@ __global__ void coarse_solve_kernel(int n, const double* __restrict__ xcm, const
   const int nI = ni * ni * ni, m = 3 * nI;
   double* rs = sm;
   double* ts = sm + m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = threadIdx.x; q < m; q += blockDim.x) {
     const int c = q / nI, iv = q % nI;
     const int i = 1 + iv % ni, j = 1 + (iv / ni) % ni, k = 1 + iv / (ni * ni);
     rs[q] = (double)r[c * V + i + (int64_t)nv * (j + (int64_t)nv * k)];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+  for (int q = warp; q < m; q += nw) {
     double s = 0.0;
-    for (int p = 0; p <= q; ++p) s = fma(xcm[(int64_t)p * m + q], rs[p], s);
-    ts[q] = s;
+    for (int p = lane; p <= q; p += 32) s = fma(xrm[(int64_t)q * m + p], rs[p], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) ts[q] = s;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+  for (int q = warp; q < m; q += nw) {
     double s = 0.0;
-    for (int p = q; p < m; ++p) s = fma(xrm[(int64_t)p * m + q], ts[p], s);
-    rs[q] = s;  // each q is read only by its own thread from here on
+    for (int p = q + lane; p < m; p += 32) s = fma(xcm[(int64_t)q * m + p], ts[p], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) rs[q] = s;
   }
   __syncthreads();
   for (int64_t id = threadIdx.x; id < 3 * V; id += blockDim.x) {
@@ -477,7 +484,7 @@ cudaError_t launch_coarse_solve(int n, const double* linv_cm, const double* linv
                                 cudaStream_t s) {
   const int ni = n - 1, m = 3 * ni * ni * ni;
   const size_t smem = 2 * (size_t)m * sizeof(double);
-  coarse_solve_kernel<T><<<1, 512, smem, s>>>(n, linv_cm, linv_rm, r, z);
+  coarse_solve_kernel<T><<<1, 1024, smem, s>>>(n, linv_cm, linv_rm, r, z);
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(int, const double*, const double*, const float*, float*, cudaStream_t);

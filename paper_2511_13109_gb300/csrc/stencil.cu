@@ -111,27 +111,56 @@ __device__ __forceinline__ void cube_stokes(const T (&Xl)[4][4], const T (&Xh)[4
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void load6(const T* p, T (&c)[6]);
-template <>
-__device__ __forceinline__ void load6<float>(const float* p, float (&c)[6]) {
-  const float2* q = reinterpret_cast<const float2*>(p);
-  float2 a = __ldg(q), b = __ldg(q + 1), d = __ldg(q + 2);
-  c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y; c[4] = d.x; c[5] = d.y;
+// cp.async (LDGSTS) helpers: asynchronous global -> shared copies, zero fill
+// when src_bytes == 0 (the source address is then not read).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes, bool ok) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int src = ok ? bytes : 0;
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src) : "memory");
 }
-template <>
-__device__ __forceinline__ void load6<double>(const double* p, double (&c)[6]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-  double2 a = __ldg(q), b = __ldg(q + 1), d = __ldg(q + 2);
-  c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y; c[4] = d.x; c[5] = d.y;
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int MODE, typename TS>
+__host__ __device__ constexpr int stencil_tile_fields() {
+  return MODE == ST_CHEB_PRE ? 6 : (MODE == ST_STOKES ? 4 : 3);
+}
+
+// dynamic shared memory of one block: tile ring [3][NF][(BX+1)(BY+1)] of TS,
+// then (128-byte aligned, as the 8/16-byte async copies need) the
+// coefficient ring [2][BX*BY][6] of T and the y-exchange [2][NC][BX*BY] of T
+template <typename TS, int BX, int BY, int MODE>
+__host__ __device__ constexpr size_t stencil_tile_bytes() {
+  return ((size_t)3 * stencil_tile_fields<MODE, TS>() * (BX + 1) * (BY + 1) * sizeof(TS) + 127) / 128 * 128;
+}
+template <typename TS, typename T, int BX, int BY, int MODE>
+__host__ __device__ constexpr size_t stencil_smem_bytes() {
+  constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;
+  return stencil_tile_bytes<TS, BX, BY, MODE>() + (size_t)2 * BX * BY * 6 * sizeof(T) +
+         (size_t)2 * NC * BX * BY * sizeof(T);
 }
 
 template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
-__global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch) {
-  constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;  // tile fields: velocity (+ fine-grid pressure)
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
+    stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch) {
+  constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;  // combined fields: velocity (+ divergence)
+  constexpr int NF = stencil_tile_fields<MODE, TS>();
+  constexpr int TW = BX + 1, TSZ = (BX + 1) * (BY + 1), NT = BX * BY;
+  constexpr int NSLOT = (TSZ + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TS* xs = reinterpret_cast<TS*>(smem_raw);
+  T* cfs = reinterpret_cast<T*>(smem_raw + stencil_tile_bytes<TS, BX, BY, MODE>());
+  T* cs = cfs + 2 * NT * 6;
+
   const int n = op.n;
   const int nv = n + 1;
   const int64_t V = (int64_t)nv * nv * nv;
+  const int64_t plane = (int64_t)nv * nv;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
   const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
@@ -139,58 +168,138 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
   const int z1 = min(z0 + zch, nv);
   const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
   const bool cube_xy = (cx >= 0) && (cx < n) && (cy >= 0) && (cy < n);
+  const int64_t cube_col = cx + (int64_t)n * cy;
   const int vx = x0 + tx, vy = y0 + ty;
   const bool owner = (tx < BX - 1) && (ty < BY - 1) && (vx < nv) && (vy < nv);
   const bool inner_xy = (vx > 0) && (vx < n) && (vy > 0) && (vy < n);
+  const int vcol = vx + nv * vy;
 
-  __shared__ T xs[NC][BY + 1][BX + 1];
-  __shared__ T cs[2][NC][BY][BX];
+  // tile slots of this thread (fixed for the whole z-march)
+  int s_col[NSLOT];
+  unsigned s_flags = 0;  // bit 2j: slot valid, 2j+1: interior in xy; bit 16+j: pressure-valid in xy
+#pragma unroll
+  for (int j = 0; j < NSLOT; ++j) {
+    const int idx = tid + j * NT;
+    const int lx = idx % TW, ly = idx / TW;
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    s_col[j] = gx + nv * gy;
+    if (idx < TSZ) {
+      s_flags |= 1u << (2 * j);
+      if (gx > 0 && gx < n && gy > 0 && gy < n) s_flags |= 2u << (2 * j);
+      if (gx >= 0 && gx <= n && gy >= 0 && gy <= n) s_flags |= 1u << (16 + j);
+    }
+  }
 
-  auto load_plane = [&](int z) {
+  const int zs = z0 - 1;
+  auto issue_tile = [&](int z) {
+    TS* dst = xs + ((z - zs) % 3) * NF * TSZ;
     const bool zin = (z > 0) && (z < n);
-    for (int idx = tid; idx < (BX + 1) * (BY + 1); idx += BX * BY) {
-      const int lx = idx % (BX + 1), ly = idx / (BX + 1);
-      const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-      const bool in = zin && gx > 0 && gx < n && gy > 0 && gy < n;
-      const int64_t v = gx + (int64_t)nv * (gy + (int64_t)nv * z);
+    const bool zq = (z >= 0) && (z <= n);
+    const int64_t pb = (int64_t)z * plane;
+#pragma unroll
+    for (int j = 0; j < NSLOT; ++j) {
+      if (!(s_flags & (1u << (2 * j)))) continue;
+      const int idx = tid + j * NT;
+      const bool in = zin && (s_flags & (2u << (2 * j)));
+      const int64_t v = in ? pb + s_col[j] : 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        T val = T(0);
-        if (in) {
-          if (MODE == ST_CHEB_PRE)
-            val = (T)(a.s2 * __ldg(a.invD + c * V + v) * __ldg(a.b + c * V + v));
-          else
-            val = (T)__ldg(a.x + c * V + v);
+        if (MODE == ST_CHEB_PRE) {
+          cp_async(dst + c * TSZ + idx, a.b + c * V + v, sizeof(TS), in);
+          cp_async(dst + (3 + c) * TSZ + idx, a.invD + c * V + v, sizeof(TS), in);
+        } else {
+          cp_async(dst + c * TSZ + idx, a.x + c * V + v, sizeof(TS), in);
         }
-        xs[c][ly][lx] = val;
       }
       if (MODE == ST_STOKES) {  // fine-grid pressure q = P p lives on every vertex
-        const bool qin = z >= 0 && z <= n && gx >= 0 && gx <= n && gy >= 0 && gy <= n;
-        xs[NC - 1][ly][lx] = qin ? (T)__ldg(a.q + v) : T(0);
+        const bool qin = zq && (s_flags & (1u << (16 + j)));
+        cp_async(dst + 3 * TSZ + idx, a.q + (qin ? pb + s_col[j] : 0), sizeof(TS), qin);
       }
     }
   };
+  auto issue_coef = [&](int kc) {
+    T* dst = cfs + (((kc - zs) & 1) * NT + tid) * 6;
+    const bool ok = cube_xy && kc >= 0 && kc < n;
+    const T* src = op.coef + (ok ? 6 * (cube_col + (int64_t)kc * n * n) : 0);
+    if (sizeof(T) == 4) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cp_async(dst + 2 * i, src + 2 * i, 8, ok);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cp_async(dst + 2 * i, src + 2 * i, 16, ok);
+    }
+  };
+  auto tile_val = [&](const TS* t, int c, int li) -> T {
+    if (MODE == ST_CHEB_PRE) return (T)(a.s2 * t[(3 + c) * TSZ + li] * t[c * TSZ + li]);
+    return (T)t[c * TSZ + li];
+  };
+
+  // prologue: planes zs, zs+1 and the coefficients of cube layer zs
+  issue_tile(zs);
+  if (zs + 1 <= n) issue_tile(zs + 1);
+  issue_coef(zs);
+  cp_commit();
 
   T Xl[4][NC], Xh[4][NC];
-  const int zs = z0 - 1;
-  load_plane(zs);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) Xl[q][c] = xs[c][ty + (q >> 1)][tx + (q & 1)];
-  __syncthreads();
-
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
+
   for (int k = zs; k < z1; ++k) {
-    if (k + 1 <= n) load_plane(k + 1);
+    // prefetch plane k+2 and the coefficients of layer k+1 while layer k computes
+    if (k + 1 < z1) {
+      if (k + 2 <= n) issue_tile(k + 2);
+      issue_coef(k + 1);
+    }
+    cp_commit();
+    // epilogue inputs of plane k, read early so their latency overlaps the compute
+    const bool out_k = owner && k >= z0;
+    const bool inner = out_k && inner_xy && k > 0 && k < n;
+    const int64_t vo = vcol + (int64_t)k * plane;
+    TS eb[3], ed[3], ep[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      eb[c] = ed[c] = ep[c] = TS(0);
+      if (inner) {
+        if (MODE == ST_RESID || MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) eb[c] = __ldg(a.b + c * V + vo);
+        if (MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) ed[c] = __ldg(a.invD + c * V + vo);
+        if (MODE == ST_CHEB_STEP) ep[c] = a.xprev[c * V + vo];
+      }
+    }
+    int32_t f[6];
+    if constexpr (COARSE) {
+      if (cube_xy && k >= 0 && k < n) {
+        const int2* fp = reinterpret_cast<const int2*>(op.fidx + 6 * (cube_col + (int64_t)k * n * n));
+        int2 f01 = __ldg(fp), f23 = __ldg(fp + 1), f45 = __ldg(fp + 2);
+        f[0] = f01.x; f[1] = f01.y; f[2] = f23.x; f[3] = f23.y; f[4] = f45.x; f[5] = f45.y;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) f[t] = -1;
+      }
+    }
+    cp_wait1();
     __syncthreads();
+    {
+      const TS* tl = xs + ((k - zs) % 3) * NF * TSZ;
+      const TS* th = xs + ((k + 1 - zs) % 3) * NF * TSZ;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q) {
+        const int li = (ty + (q >> 1)) * TW + tx + (q & 1);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) Xh[q][c] = (k + 1 <= n) ? xs[c][ty + (q >> 1)][tx + (q & 1)] : T(0);
+        for (int c = 0; c < NC; ++c) {
+          if (k == zs) Xl[q][c] = (c < 3) ? tile_val(tl, c, li) : (T)tl[c * TSZ + li];
+          Xh[q][c] = (k + 1 <= n) ? ((c < 3) ? tile_val(th, c, li) : (T)th[c * TSZ + li]) : T(0);
+        }
+      }
+      if (MODE == ST_CHEB_PRE && inner) {  // own b and D^-1 on plane k, before the ring slot is reused
+        const int li = (ty + 1) * TW + tx + 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          eb[c] = tl[c * TSZ + li];
+          ed[c] = tl[(3 + c) * TSZ + li];
+        }
+      }
+    }
 
     T Y[8][NC];
 #pragma unroll
@@ -199,40 +308,23 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
       for (int c = 0; c < NC; ++c) Y[q][c] = T(0);
 
     if (cube_xy && k >= 0 && k < n) {
-      const int64_t cube = cx + (int64_t)n * (cy + (int64_t)n * k);
+      const T* cp = cfs + (((k - zs) & 1) * NT + tid) * 6;
       T cf[6];
-      load6<T>(op.coef + 6 * cube, cf);
 #pragma unroll
-      for (int t = 0; t < 6; ++t) cf[t] *= op.h6;
+      for (int t = 0; t < 6; ++t) cf[t] = cp[t] * op.h6;
       if constexpr (COARSE) {
-        int32_t f[6];
-        const int2* fp = reinterpret_cast<const int2*>(op.fidx + 6 * cube);
-        int2 f01 = __ldg(fp), f23 = __ldg(fp + 1), f45 = __ldg(fp + 2);
-        f[0] = f01.x; f[1] = f01.y; f[2] = f23.x; f[3] = f23.y; f[4] = f45.x; f[5] = f45.y;
 #pragma unroll
         for (int t = 0; t < 6; ++t)
           if (f[t] >= 0) cf[t] = T(0);
         cube_dca<T, NC>(Xl, Xh, cf, Y);
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
-          if (f[t] >= 0) {
-            const T* M = op.gca + (int64_t)f[t] * 144;
-            const T sc = op.gscale ? op.gscale[f[t]] : T(1);
-            T xl[12];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const int q = tet_corner(t, b);
-                xl[d * 4 + b] = (q & 4) ? Xh[q & 3][d] : Xl[q & 3][d];
-              }
+          if (f[t] >= 0) {  // stored Galerkin element: s_e A_e x_e precomputed by gca_apply_kernel
+            const T* yv = op.ye + (int64_t)f[t] * 12;
 #pragma unroll
             for (int r = 0; r < 12; ++r) {
-              T yr = T(0);
-#pragma unroll
-              for (int s2 = 0; s2 < 12; ++s2) yr = fma(M[r * 12 + s2], xl[s2], yr);
               const int q = tet_corner(t, r & 3);
-              Y[q][r >> 2] = fma(sc, yr, Y[q][r >> 2]);
+              Y[q][r >> 2] += yv[r];
             }
           }
         }
@@ -252,8 +344,8 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
         // corners (qx, qy, qz): index qx + 2 qy + 4 qz
         const T from_right_y1 = __shfl_down_sync(0xffffffffu, Y[4 * qz + 2][c], 1);
         const T from_right_y0 = __shfl_down_sync(0xffffffffu, Y[4 * qz + 0][c], 1);
-        s1[qz][c] = Y[4 * qz + 3][c] + from_right_y1;           // row qy = 1 (own vertex row)
-        cs[qz][c][ty][tx] = Y[4 * qz + 1][c] + from_right_y0;   // row qy = 0, for thread ty-1
+        s1[qz][c] = Y[4 * qz + 3][c] + from_right_y1;                        // row qy = 1 (own vertex row)
+        cs[((qz & 1) * NC + c) * NT + tid] = Y[4 * qz + 1][c] + from_right_y0;  // row qy = 0, for thread ty-1
       }
     __syncthreads();
 
@@ -261,15 +353,13 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
       T yk[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        yk[c] = acc[c] + (s1[0][c] + cs[0][c][ty + 1][tx]);
-        acc[c] = s1[1][c] + cs[1][c][ty + 1][tx];
+        yk[c] = acc[c] + (s1[0][c] + cs[c * NT + tid + BX]);
+        acc[c] = s1[1][c] + cs[(NC + c) * NT + tid + BX];
       }
-      if (k >= z0) {
-        const int64_t v = vx + (int64_t)nv * (vy + (int64_t)nv * k);
-        const bool inner = inner_xy && k > 0 && k < n;
+      if (out_k) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int64_t i = c * V + v;
+          const int64_t i = c * V + vo;
           TS o = TS(0);
           if (inner) {
             const TS xo = (TS)Xl[3][c];  // own vertex value on plane k
@@ -277,19 +367,18 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
             if (MODE == ST_APPLY || MODE == ST_STOKES) {
               o = y;
             } else if (MODE == ST_RESID) {
-              o = __ldg(a.b + i) - y;
+              o = eb[c] - y;
             } else if (MODE == ST_CHEB_FIRST) {
-              o = xo + a.s0 * __ldg(a.invD + i) * (__ldg(a.b + i) - y);
+              o = xo + a.s0 * ed[c] * (eb[c] - y);
             } else if (MODE == ST_CHEB_STEP) {
-              const TS xp = a.xprev[i];
-              o = xo + a.s0 * (xo - xp) + a.s1 * __ldg(a.invD + i) * (__ldg(a.b + i) - y);
+              o = xo + a.s0 * (xo - ep[c]) + a.s1 * ed[c] * (eb[c] - y);
             } else {  // ST_CHEB_PRE: x1 = s2 D^-1 b staged in the tile, x0 = 0
-              o = xo + a.s0 * xo + a.s1 * __ldg(a.invD + i) * (__ldg(a.b + i) - y);
+              o = xo + a.s0 * xo + a.s1 * ed[c] * (eb[c] - y);
             }
           }
           a.out[i] = o;
         }
-        if (MODE == ST_STOKES) a.out2[v] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
+        if (MODE == ST_STOKES) a.out2[vo] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
       }
     }
 #pragma unroll
@@ -299,28 +388,96 @@ __global__ void __launch_bounds__(BX* BY) stencil_kernel(const LevelOp<T> op, co
   }
 }
 
+// Flagged elements of a coarse level: y_e = s_e A_e x_e (Eq. 2.9, stored
+// Galerkin part), one thread per (element, row), written to op.ye for the
+// stencil kernel to scatter.  x follows the stencil's input convention
+// (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).
+template <typename TS, typename T, bool PRE>
+__global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= op.n_flag * 12) return;
+  const int64_t f = id / 12;
+  const int r = (int)(id % 12);
+  const int64_t e = op.list[f];
+  const int t = (int)(e % 6);
+  const int64_t cube = e / 6;
+  const int n = op.n, nv = n + 1;
+  const int64_t V = (int64_t)nv * nv * nv;
+  const int ci = (int)(cube % n), cj = (int)((cube / n) % n), ck = (int)(cube / ((int64_t)n * n));
+  const T* M = op.gca + f * 144 + r * 12;
+  T acc = T(0);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int q = tet_corner(t, b);
+    const int i = ci + (q & 1), j = cj + ((q >> 1) & 1), k = ck + ((q >> 2) & 1);
+    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
+    const int64_t v = i + (int64_t)nv * (j + (int64_t)nv * k);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T xv = T(0);
+      if (inner) {
+        if (PRE)
+          xv = (T)(a.s2 * __ldg(a.invD + d * V + v) * __ldg(a.b + d * V + v));
+        else
+          xv = (T)__ldg(a.x + d * V + v);
+      }
+      acc = fma(M[d * 4 + b], xv, acc);
+    }
+  }
+  op.ye[f * 12 + r] = op.gscale ? op.gscale[f] * acc : acc;
+}
+
 template <typename TS, typename T, int BX, int BY, bool COARSE>
 cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s) {
   const int nv = op.n + 1;
   const int gx = (nv + BX - 2) / (BX - 1), gy = (nv + BY - 2) / (BY - 1);
-  int gz = (608 + gx * gy - 1) / (gx * gy);
+  // enough blocks for two waves of 3 resident blocks per SM; small grids get
+  // short z-chunks (latency bound), large ones long chunks (less z-halo)
+  int gz = (912 + gx * gy - 1) / (gx * gy);
   int zch = (nv + gz - 1) / gz;
-  if (zch < 4) zch = 4;
+  if (zch < 1) zch = 1;
   if (zch > nv) zch = nv;
   gz = (nv + zch - 1) / zch;
+  if (COARSE && op.n_flag > 0) {
+    const int64_t nth = op.n_flag * 12;
+    const unsigned gb = (unsigned)((nth + 127) / 128);
+    if (mode == ST_CHEB_PRE)
+      gca_apply_kernel<TS, T, true><<<gb, 128, 0, s>>>(op, a);
+    else
+      gca_apply_kernel<TS, T, false><<<gb, 128, 0, s>>>(op, a);
+  }
   dim3 grid(gx, gy, gz), block(BX, BY);
+#define AGCA_LAUNCH(M, C)                                                                                  \
+  do {                                                                                                     \
+    constexpr size_t smem = stencil_smem_bytes<TS, T, BX, BY, M>();                                       \
+    static bool attr_set[64] = {};                                                                        \
+    int dev_ = 0;                                                                                         \
+    cudaError_t e = cudaGetDevice(&dev_);                                                                 \
+    if (e != cudaSuccess) return e;                                                                       \
+    if (smem > 48 * 1024 && dev_ >= 0 && dev_ < 64 && !attr_set[dev_]) {                                  \
+      e = cudaFuncSetAttribute(stencil_kernel<TS, T, BX, BY, M, C>,                                       \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
+      if (e != cudaSuccess) return e;                                                                     \
+      attr_set[dev_] = true;                                                                              \
+    }                                                                                                     \
+    stencil_kernel<TS, T, BX, BY, M, C><<<grid, block, smem, s>>>(op, a, zch);                            \
+  } while (0)
   switch (mode) {
-    case ST_APPLY: stencil_kernel<TS, T, BX, BY, ST_APPLY, COARSE><<<grid, block, 0, s>>>(op, a, zch); break;
-    case ST_RESID: stencil_kernel<TS, T, BX, BY, ST_RESID, COARSE><<<grid, block, 0, s>>>(op, a, zch); break;
-    case ST_CHEB_FIRST: stencil_kernel<TS, T, BX, BY, ST_CHEB_FIRST, COARSE><<<grid, block, 0, s>>>(op, a, zch); break;
-    case ST_CHEB_STEP: stencil_kernel<TS, T, BX, BY, ST_CHEB_STEP, COARSE><<<grid, block, 0, s>>>(op, a, zch); break;
-    case ST_CHEB_PRE: stencil_kernel<TS, T, BX, BY, ST_CHEB_PRE, COARSE><<<grid, block, 0, s>>>(op, a, zch); break;
+    case ST_APPLY: AGCA_LAUNCH(ST_APPLY, COARSE); break;
+    case ST_RESID: AGCA_LAUNCH(ST_RESID, COARSE); break;
+    case ST_CHEB_FIRST: AGCA_LAUNCH(ST_CHEB_FIRST, COARSE); break;
+    case ST_CHEB_STEP: AGCA_LAUNCH(ST_CHEB_STEP, COARSE); break;
+    case ST_CHEB_PRE: AGCA_LAUNCH(ST_CHEB_PRE, COARSE); break;
     case ST_STOKES:
-      if (COARSE) return cudaErrorInvalidValue;
-      stencil_kernel<TS, T, BX, BY, ST_STOKES, false><<<grid, block, 0, s>>>(op, a, zch);
+      if constexpr (COARSE) {
+        return cudaErrorInvalidValue;
+      } else {
+        AGCA_LAUNCH(ST_STOKES, false);
+      }
       break;
     default: return cudaErrorInvalidValue;
   }
+#undef AGCA_LAUNCH
   return cudaGetLastError();
 }
 
