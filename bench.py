@@ -78,10 +78,13 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.proc = None
+        self.first = ""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
                  "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            # nvidia-smi's start-up (NVML initialisation) must not overlap the timed region
+            self.first = self.proc.stdout.readline()
         except OSError:
             self.proc = None
 
@@ -96,7 +99,7 @@ class ClockSampler:
             out, _ = self.proc.communicate()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in (self.first + out).strip().splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -185,6 +188,69 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, dev, stream):
+    """The 24-problem batch (uneven 32^3/48^3/64^3 sinkers): batched V-cycle
+    throughput against the same problems cycled one by one, and batched solve
+    time to 1e-8 against sequential solves."""
+    import paper_2511_13109_gb300 as pkg
+    from synth import batch_problems
+
+    probs = batch_problems(device=dev)
+    if args.batch_n:
+        probs = probs[:args.batch_n]
+    etas = [torch.from_numpy(p.eta).to(dev) for p in probs]
+    fbars = [torch.from_numpy(p.fbar.ravel()).to(dev) for p in probs]
+    out = {"problems": len(probs), "sizes": [p.N for p in probs]}
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        b = pkg.Batch([p.N for p in probs], pkg.MIXED, device=dev, stream=stream)
+        b.prepare(etas, 10.0)
+        stream.synchronize()
+        out["setup_s"] = time.perf_counter() - t0
+        rs = [torch.rand(3 * c.V[c.L], dtype=torch.float64, device=dev) * 2 - 1 for c in b.contexts]
+        zs = [torch.empty_like(r) for r in rs]
+        dofs = sum(3 * c.V[c.L] for c in b.contexts)
+        for _ in range(3):
+            b.vcycle(rs, zs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 20
+        e0.record(stream)
+        for _ in range(k):
+            b.vcycle(rs, zs)
+        e1.record(stream)
+        e1.synchronize()
+        out["batched_vcycle_dofs_per_s"] = dofs / (e0.elapsed_time(e1) / k * 1e-3)
+        singles = []
+        for p, eta in zip(probs, etas):
+            c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.MIXED, device=dev, stream=stream)
+            c.prepare(eta, 10.0)
+            singles.append(c)
+        for c, r, z in zip(singles, rs, zs):
+            c.vcycle(r, z)
+        e0.record(stream)
+        for _ in range(k):
+            for c, r, z in zip(singles, rs, zs):
+                c.vcycle(r, z)
+        e1.record(stream)
+        e1.synchronize()
+        out["sequential_vcycle_dofs_per_s"] = dofs / (e0.elapsed_time(e1) / k * 1e-3)
+        if not args.no_solve:
+            bs = [b.load_vector(i, f) for i, f in enumerate(fbars)]
+            stream.synchronize()
+            t0 = time.perf_counter()
+            xs, its, rel = b.solve(bs, 1e-8, 40000)
+            stream.synchronize()
+            out["batched_solve_s"] = time.perf_counter() - t0
+            out["batched_iters"] = its
+            out["batched_max_relres"] = max(rel)
+            t0 = time.perf_counter()
+            for c, bb in zip(singles, bs):
+                c.solve(bb, 1e-8, 40000)
+            stream.synchronize()
+            out["sequential_solve_s"] = time.perf_counter() - t0
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +260,9 @@ def main():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="also run the 24-problem batch")
+    ap.add_argument("--batch-n", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -220,6 +289,9 @@ def main():
     with torch.cuda.stream(stream):
         ctx = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
         ctx.prepare(eta, prm["nu"])
+        t_tune = time.perf_counter()
+        tuned = ctx.autotune(reps=10) if not args.no_tune else {}
+        t_tune = time.perf_counter() - t_tune
         n3 = 3 * ctx.V[L]
         g = torch.Generator(device=dev)
         g.manual_seed(1234 + rank)
@@ -230,7 +302,6 @@ def main():
         stream.synchronize()
         _barrier(dist)
         clocks = ClockSampler(local)
-        time.sleep(0.3)
         launches0 = ctx.launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -316,6 +387,8 @@ def main():
                 solve[name] = {"time_to_1e-8_s": tot, "setup_s": st, "solve_s": sv, "minres_iters": its,
                                "relres": rel}
 
+    batch = run_batch(args, dev, stream) if args.batch else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, k, dt, cores = oracle_vcycle_rate(12.0)
@@ -344,7 +417,9 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "fp64_vcycle": {"value": dofs / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms},
+            "autotune": {"seconds": t_tune, "tiles": {f"L{l}m{m}": list(v) for (l, m), v in tuned.items()}},
             "solve": solve,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -99,7 +99,7 @@ const char* agca_last_error(const agca_ctx* ctx);
 
 /* Smoother parameters (Section 4: Chebyshev smoother on D^-1 A): polynomial
  * degree, interval [lo, hi] * lambda_hat and the number of power iterations
- * for lambda_hat.  Defaults 2, 0.3, 1.2, 20.  Call before agca_setup. */
+ * for lambda_hat.  Defaults 2, 0.1, 1.1, 20.  Call before agca_setup. */
 agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, int power_iters);
 
 /* Bytes of device workspace the context needs (excluding the Galerkin store). */
@@ -193,6 +193,17 @@ agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const doub
 agca_status agca_stokes_apply_static(int N, const double* eta_dev, const double* x_dev, double* y_dev,
                                      void* cuda_stream);
 
+/* Autotuner: for every level >= 2 and V-cycle stencil mode (0 apply,
+ * 1 residual, 2 first and 3 later Chebyshev steps, 4 pre-smoothing step from
+ * zero), time the candidate tile shapes (block rows 8/12/16 in FP32, 8 in
+ * FP64; z-chunks 1..64) with CUDA events on the context stream, reps
+ * launches each, and keep the fastest for the context's later launches.
+ * cache_path (nullable): text file of earlier results, read first and
+ * rewritten.  Uses the cycle vectors as scratch.  Synchronizes. */
+agca_status agca_autotune(agca_ctx* ctx, int reps, const char* cache_path);
+/* The tile shape in use for (level, mode): block rows and z-chunk (0 = automatic). */
+agca_status agca_tile_config(const agca_ctx* ctx, int level, int mode, int* by, int* zch);
+
 /* Number of CUDA kernels this context has launched so far (host counter). */
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
 /* Per-launch timing of the finest-level stencil kernels (the dominant
@@ -203,6 +214,46 @@ agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
  * and the number of timed launches.  Output pointers are host pointers and
  * may be NULL when enabling. */
 agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, int64_t* launches);
+
+/* ------------------------------------------------------------------------
+ * Batched solves of many independent problems (uneven sizes allowed).
+ * Every problem keeps its own hierarchy; the MINRES iterations of all
+ * problems run in lockstep, each launch covering every problem: the stencil
+ * launches are persistent (every CTA walks the flattened (problem, tile)
+ * work list) and one lockstep iteration pair is captured once as a CUDA graph
+ * (when the stream is not the legacy default stream) and replayed.
+ * Converged problems are skipped on the device.  The batch owns its
+ * sub-contexts; device memory is bound by the caller as for one context.
+ * ---------------------------------------------------------------------- */
+typedef struct agca_batch agca_batch;
+/* n problems with Ns[i] pressure cubes per axis, default level counts
+ * (coarsen while the velocity grid stays even with >= 4 cubes), one
+ * precision for all; degree-2 Chebyshev smoothing. */
+agca_status agca_batch_create(int n, const int* Ns, int prec, void* cuda_stream, agca_batch** out);
+void agca_batch_destroy(agca_batch* b);
+const char* agca_batch_last_error(const agca_batch* b);
+agca_status agca_batch_workspace_size(const agca_batch* b, size_t* bytes);
+agca_status agca_batch_bind_workspace(agca_batch* b, void* dev_ptr, size_t bytes);
+/* as agca_set_viscosity for problem i */
+agca_status agca_batch_set_viscosity(agca_batch* b, int i, const double* eta_dev);
+/* as agca_flag for every problem; *gca_bytes: the total Galerkin store */
+agca_status agca_batch_flag(agca_batch* b, double nu, size_t* gca_bytes);
+agca_status agca_batch_bind_gca_store(agca_batch* b, void* dev_ptr, size_t bytes);
+/* as agca_setup for every problem, then builds the batched task tables and
+ * captures the lockstep iteration graph.  Synchronizes. */
+agca_status agca_batch_setup(agca_batch* b);
+/* as agca_load_vector for problem i */
+agca_status agca_batch_load_vector(agca_batch* b, int i, const double* fbar_dev, double* b_dev);
+/* One V-cycle for every problem: z_devs[i] = V_i(r_devs[i]) (host arrays of
+ * n device pointers).  Synchronizes. */
+agca_status agca_batch_vcycle(agca_batch* b, const double* const* r_devs, double* const* z_devs);
+/* Solve every problem to ||b_i - K_i x_i|| <= rtol ||b_i|| (as agca_solve);
+ * iters, relres: host arrays of n (may be NULL).  Synchronizes. */
+agca_status agca_batch_solve(agca_batch* b, const double* const* b_devs, double* const* x_devs, double rtol, int maxit,
+                             int* iters, double* relres);
+/* The context of problem i (owned by the batch): parity hooks such as
+ * agca_get_level_data, agca_apply, agca_level_info. */
+agca_ctx* agca_batch_context(agca_batch* b, int i);
 
 /* Level metadata (host struct).  Synchronizes. */
 agca_status agca_level_info(agca_ctx* ctx, int level, agca_level_info_t* out);

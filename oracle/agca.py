@@ -54,7 +54,7 @@ def pairwise8(c: np.ndarray) -> np.ndarray:
 
 class Hierarchy:
     def __init__(self, N: int, L: int, eta: np.ndarray, nu: float = 10.0,
-                 cheb_lo: float = 0.3, cheb_hi: float = 1.2, cheb_degree: int = 2,
+                 cheb_lo: float = 0.1, cheb_hi: float = 1.1, cheb_degree: int = 2,
                  power_iters: int = 20, build_operators: bool = True):
         nL = 2 * N
         assert nL % (1 << (L - 1)) == 0 and (nL >> (L - 1)) >= 2

@@ -20,6 +20,7 @@ from .agca import (  # noqa: F401
     FP64,
     MIXED,
     AgcaError,
+    Batch,
     Context,
     default_levels,
     exported_symbols,

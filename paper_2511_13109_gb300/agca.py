@@ -63,8 +63,24 @@ _SIGS = {
     "agca_element_sensitivity": ([_P, _P, _P, _P], _I),
     "agca_adjoint_gradient": ([_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I)], _I),
     "agca_stokes_apply_static": ([_I, _P, _P, _P, _P], _I),
+    "agca_autotune": ([_P, _I, ctypes.c_char_p], _I),
+    "agca_tile_config": ([_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
+    "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
+    "agca_batch_destroy": ([_P], None),
+    "agca_batch_last_error": ([_P], ctypes.c_char_p),
+    "agca_batch_workspace_size": ([_P, ctypes.POINTER(_SZ)], _I),
+    "agca_batch_bind_workspace": ([_P, _P, _SZ], _I),
+    "agca_batch_set_viscosity": ([_P, _I, _P], _I),
+    "agca_batch_flag": ([_P, _D, ctypes.POINTER(_SZ)], _I),
+    "agca_batch_bind_gca_store": ([_P, _P, _SZ], _I),
+    "agca_batch_setup": ([_P], _I),
+    "agca_batch_load_vector": ([_P, _I, _P, _P], _I),
+    "agca_batch_vcycle": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
+    "agca_batch_solve": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_I),
+                          ctypes.POINTER(_D)], _I),
+    "agca_batch_context": ([_P, _I], _P),
     "agca_level_info": ([_P, _I, ctypes.POINTER(LevelInfo)], _I),
     "agca_get_level_data": ([_P, _I, _I, _P], _I),
 }
@@ -156,9 +172,25 @@ class Context:
         self.Vp = (N + 1) ** 3
         self.nt = 3 * self.V[self.L] + self.Vp
 
+    @classmethod
+    def _borrowed(cls, handle, N, levels, precision, device, stream, owner):
+        """View of a context owned by a batch (not destroyed by this object)."""
+        self = cls.__new__(cls)
+        self.N, self.L, self.precision = N, levels, precision
+        self.device, self.stream = torch.device(device), stream
+        self._h = handle
+        self._owner = owner
+        self.workspace = self.gca_store = None
+        self.nL = 2 * N
+        self.V = {l: (((self.nL >> (self.L - l)) + 1) ** 3) for l in range(1, self.L + 1)}
+        self.E = {l: 6 * (self.nL >> (self.L - l)) ** 3 for l in range(1, self.L + 1)}
+        self.Vp = (N + 1) ** 3
+        self.nt = 3 * self.V[self.L] + self.Vp
+        return self
+
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
+        if h is not None and _lib is not None and getattr(self, "_owner", None) is None:
             _lib.agca_destroy(h)
             self._h = None
 
@@ -171,7 +203,7 @@ class Context:
         return torch.float64 if dtype == F64 else torch.float32
 
     # ---- setup ---------------------------------------------------------------
-    def set_smoother(self, degree=2, lo=0.3, hi=1.2, power_iters=20):
+    def set_smoother(self, degree=2, lo=0.1, hi=1.1, power_iters=20):
         self._check(lib().agca_set_smoother(self._h, degree, lo, hi, power_iters), "set_smoother")
 
     def set_viscosity(self, eta: torch.Tensor):
@@ -272,6 +304,18 @@ class Context:
         return g, its.value
 
     # ---- introspection ---------------------------------------------------------
+    def autotune(self, reps: int = 10, cache: str | None = None) -> dict:
+        """Pick the tile shape of every V-cycle stencil launch by timing
+        (agca_autotune); returns {(level, mode): (block_rows, z_chunk)}."""
+        self._check(lib().agca_autotune(self._h, int(reps), cache.encode() if cache else None), "autotune")
+        out = {}
+        for l in range(2, self.L + 1):
+            for mode in (1, 2, 3, 4):
+                by, zc = _I(), _I()
+                self._check(lib().agca_tile_config(self._h, l, mode, ctypes.byref(by), ctypes.byref(zc)), "tile_config")
+                out[(l, mode)] = (by.value, zc.value)
+        return out
+
     def launch_count(self) -> int:
         n = ctypes.c_int64()
         self._check(lib().agca_launch_count(self._h, ctypes.byref(n)), "launch_count")
@@ -301,3 +345,79 @@ class Context:
         out = torch.empty(max(1, shape[0]), dtype=shape[1], device=self.device)
         self._check(lib().agca_get_level_data(self._h, level, field, _ptr(out)), "get_level_data")
         return out[:shape[0]]
+
+
+class Batch:
+    """Many independent problems solved in lockstep (agca_batch_*)."""
+
+    def __init__(self, Ns, precision: int = MIXED, device="cuda", stream: torch.cuda.Stream | None = None):
+        self.Ns = [int(n) for n in Ns]
+        self.n = len(self.Ns)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = _P()
+        arr = (_I * self.n)(*self.Ns)
+        st = lib().agca_batch_create(self.n, arr, precision, _P(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise AgcaError(st, f"agca_batch_create({self.Ns})")
+        self._h = h
+        sz = _SZ()
+        self._check(lib().agca_batch_workspace_size(self._h, ctypes.byref(sz)), "workspace_size")
+        self.workspace = torch.empty(int(sz.value), dtype=torch.uint8, device=self.device)
+        self._check(lib().agca_batch_bind_workspace(self._h, _ptr(self.workspace), sz.value), "bind_workspace")
+        self.gca_store = None
+        self.contexts = [Context._borrowed(lib().agca_batch_context(self._h, i), N, default_levels(N), precision,
+                                           self.device, self.stream, self) for i, N in enumerate(self.Ns)]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            for c in getattr(self, "contexts", []):
+                c._h = None
+            _lib.agca_batch_destroy(h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st != 0:
+            raise AgcaError(st, f"{what}: {lib().agca_batch_last_error(self._h).decode()}")
+
+    def prepare(self, etas, nu: float = 10.0):
+        for i, eta in enumerate(etas):
+            _need(eta, self.contexts[i].E[self.contexts[i].L], torch.float64, f"eta[{i}]")
+            self._check(lib().agca_batch_set_viscosity(self._h, i, _ptr(eta)), "set_viscosity")
+        b = _SZ()
+        self._check(lib().agca_batch_flag(self._h, float(nu), ctypes.byref(b)), "flag")
+        self.gca_store = torch.empty(max(256, int(b.value)), dtype=torch.uint8, device=self.device)
+        self._check(lib().agca_batch_bind_gca_store(self._h, _ptr(self.gca_store), b.value), "bind_gca_store")
+        self._check(lib().agca_batch_setup(self._h), "setup")
+
+    def load_vector(self, i: int, fbar: torch.Tensor):
+        c = self.contexts[i]
+        _need(fbar, 3 * c.E[c.L], torch.float64, "fbar")
+        b = torch.empty(c.nt, dtype=torch.float64, device=self.device)
+        self._check(lib().agca_batch_load_vector(self._h, i, _ptr(fbar), _ptr(b)), "load_vector")
+        return b
+
+    def vcycle(self, rs, zs=None):
+        zs = [torch.empty_like(r) for r in rs] if zs is None else zs
+        for i, (r, z) in enumerate(zip(rs, zs)):
+            n = 3 * self.contexts[i].V[self.contexts[i].L]
+            _need(r, n, torch.float64, f"r[{i}]")
+            _need(z, n, torch.float64, f"z[{i}]")
+        ra = (_P * self.n)(*[r.data_ptr() for r in rs])
+        za = (_P * self.n)(*[z.data_ptr() for z in zs])
+        self._check(lib().agca_batch_vcycle(self._h, ra, za), "vcycle")
+        return zs
+
+    def solve(self, bs, rtol: float = 1e-8, maxit: int = 20000, xs=None):
+        xs = [torch.empty_like(b) for b in bs] if xs is None else xs
+        for i, (b, x) in enumerate(zip(bs, xs)):
+            _need(b, self.contexts[i].nt, torch.float64, f"b[{i}]")
+            _need(x, self.contexts[i].nt, torch.float64, f"x[{i}]")
+        ba = (_P * self.n)(*[b.data_ptr() for b in bs])
+        xa = (_P * self.n)(*[x.data_ptr() for x in xs])
+        its = (_I * self.n)()
+        rel = (_D * self.n)()
+        self._check(lib().agca_batch_solve(self._h, ba, xa, float(rtol), int(maxit), its, rel), "solve")
+        return xs, list(its), list(rel)

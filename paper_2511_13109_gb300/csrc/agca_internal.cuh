@@ -99,9 +99,54 @@ struct StencilArgs {
   T s0, s1, s2;    // mode scalars
 };
 
+// Tile shape of a stencil launch: block rows BY (8, 12 or 16 for FP32; 8
+// otherwise) and the z-chunk (0 = automatic).  Chosen by the autotuner.
+struct TileCfg {
+  int by = 8;
+  int zch = 0;
+};
+
 // TS: storage type of the vectors; T: compute type (and type of the level data)
 template <typename TS, typename T>
-cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s);
+cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s,
+                           const TileCfg* cfg = nullptr);
+
+// ------------------------------------------------------------ batched forms
+// One (problem, level) operator application inside a batched launch.
+template <typename TS, typename T>
+struct StencilTask {
+  LevelOp<T> op;
+  StencilArgs<TS> a;
+  int zch, gx, gy, gz;
+  int64_t tile0;        // first tile of this task in the flattened work list
+  const double* sc;     // MINRES scalars of the problem (skip when sc[MS_DONE] != 0) or nullptr
+};
+// tile decomposition used by both the single and the batched launch
+void stencil_grid(int n, int* gx, int* gy, int* gz, int* zch);
+void stencil_grid_by(int n, int by, int zch_req, int* gx, int* gy, int* gz, int* zch);
+// tasks: device array, ntiles = total tiles; launches the gca_apply part too
+// when coarse (gtasks: the same tasks, one per problem with flagged elements)
+template <typename TS, typename T>
+cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
+                                 int64_t max_gca_rows, cudaStream_t s);
+
+// Element-wise batched tasks (transfers, conversions, coarsest solves).
+struct XferTask {
+  int nf;               // fine cubes per axis (transfers) or cubes per axis (coarse solve)
+  int ncomp;            // components (transfers)
+  int mask;             // zero Dirichlet rows (transfers)
+  double scale;         // restriction scale
+  int64_t count;        // work items of the task
+  const void* src;
+  void* dst;
+  const double* m1;     // coarsest solve: L^-1 column-major
+  const double* m2;     // coarsest solve: L^-1 row-major
+  const double* sc;     // skip when sc[MS_DONE] != 0, or nullptr
+};
+enum XferKind { XK_RESTRICT = 0, XK_PROLONG_ADD, XK_D2F, XK_F2D, XK_COARSE, XK_PROLONG, XK_COPY64 };
+template <typename T>
+cudaError_t launch_xfer_batch(int kind, const XferTask* tasks, int ntasks, int64_t max_count, int max_m,
+                              cudaStream_t s);
 
 // grid transfers (transfer.cu)
 template <typename T>
@@ -155,6 +200,20 @@ cudaError_t launch_minres_scalars(double* sc, cudaStream_t s);
 cudaError_t launch_minres_update(int64_t n, const double* z, const double* w, double* wold_to_wnew, double* x,
                                  const double* sc, cudaStream_t s);
 cudaError_t launch_load_vector(int n, const double* fbar, double* b, cudaStream_t s);
+// batched MINRES pieces: one task per problem (pointers per problem)
+struct KTask {
+  int64_t n;            // vector length
+  double* sc;           // MINRES scalars of the problem
+  const double* a;
+  const double* b;
+  double* c;
+  double* d;
+  int slot;             // scalar slot written by reductions
+  double scale;         // reduction scale
+};
+enum KBatchOp { KB_DOT = 0, KB_SUM, KB_LANCZOS, KB_UPDATE, KB_SCALARS, KB_PDIV, KB_SUBS };
+cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t max_n, double* partials,
+                                cudaStream_t s);
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s);
 cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
                                cudaStream_t s);

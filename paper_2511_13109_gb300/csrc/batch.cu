@@ -1,0 +1,297 @@
+// Batched element-wise kernels: many independent problems per launch.
+// Grid (chunks, problems): block row y serves problem y, blocks past the end
+// of a smaller problem exit at once.  A problem whose MINRES has converged
+// (sc[MS_DONE] != 0) is skipped.  Used by the batched solve of
+// agca_batch_solve (persistent stencil launches live in stencil.cu).
+#include <math.h>
+
+#include <algorithm>
+
+#include "agca_internal.cuh"
+
+namespace agca {
+
+namespace {
+
+constexpr int kBT = 256;
+constexpr int kDotBlocks = 64;  // per problem: fixed, so the reductions are deterministic
+
+__device__ __forceinline__ bool skip(const double* sc) { return sc && sc[MS_DONE] != 0.0; }
+
+template <typename T>
+__global__ void restrict_batch_kernel(const XferTask* __restrict__ tasks) {
+  const XferTask tk = tasks[blockIdx.y];
+  if (skip(tk.sc)) return;
+  const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
+  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= Vc) return;
+  const T* rf = static_cast<const T*>(tk.src);
+  T* rc = static_cast<T*>(tk.dst);
+  const int I = (int)(id % nvc), J = (int)((id / nvc) % nvc), K = (int)(id / ((int64_t)nvc * nvc));
+  const bool bd = I == 0 || J == 0 || K == 0 || I == nc || J == nc || K == nc;
+  for (int c = 0; c < tk.ncomp; ++c) {
+    T out = T(0);
+    if (!(tk.mask && bd)) {
+      const T* r = rf + c * Vf;
+      const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
+      T acc = T(0);
+#pragma unroll
+      for (int d = 1; d < 8; ++d) {
+        const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+        if (fi + dx <= nf && fj + dy <= nf && fk + dz <= nf)
+          acc += r[(fi + dx) + (int64_t)nvf * ((fj + dy) + (int64_t)nvf * (fk + dz))];
+        if (fi - dx >= 0 && fj - dy >= 0 && fk - dz >= 0)
+          acc += r[(fi - dx) + (int64_t)nvf * ((fj - dy) + (int64_t)nvf * (fk - dz))];
+      }
+      out = (T)tk.scale * (r[fi + (int64_t)nvf * (fj + (int64_t)nvf * fk)] + T(0.5) * acc);
+    }
+    rc[c * Vc + id] = out;
+  }
+}
+
+template <typename T, bool ADD>
+__global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
+  const XferTask tk = tasks[blockIdx.y];
+  if (skip(tk.sc)) return;
+  const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
+  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= Vf) return;
+  const T* ec = static_cast<const T*>(tk.src);
+  T* xf = static_cast<T*>(tk.dst);
+  const int i = (int)(id % nvf), j = (int)((id / nvf) % nvf), k = (int)(id / ((int64_t)nvf * nvf));
+  const bool bd = i == 0 || j == 0 || k == 0 || i == nf || j == nf || k == nf;
+  const int I = i >> 1, J = j >> 1, K = k >> 1, dx = i & 1, dy = j & 1, dz = k & 1;
+  const int64_t c0 = I + (int64_t)nvc * (J + (int64_t)nvc * K);
+  const int64_t c1 = (I + dx) + (int64_t)nvc * ((J + dy) + (int64_t)nvc * (K + dz));
+  const bool odd = dx | dy | dz;
+  for (int c = 0; c < tk.ncomp; ++c) {
+    const T* e = ec + c * Vc;
+    T v = odd ? T(0.5) * (e[c0] + e[c1]) : e[c0];
+    if (tk.mask && bd) v = T(0);
+    if (ADD)
+      xf[c * Vf + id] += v;
+    else
+      xf[c * Vf + id] = v;
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_batch_kernel(const XferTask* __restrict__ tasks) {
+  const XferTask tk = tasks[blockIdx.y];
+  if (skip(tk.sc)) return;
+  const TI* in = static_cast<const TI*>(tk.src);
+  TO* out = static_cast<TO*>(tk.dst);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tk.count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+// coarsest solves, one block per problem (as coarse_solve_kernel)
+template <typename T>
+__global__ void coarse_solve_batch_kernel(const XferTask* __restrict__ tasks) {
+  extern __shared__ double sm[];
+  const XferTask tk = tasks[blockIdx.x];
+  if (skip(tk.sc)) return;
+  const int n = tk.nf, nv = n + 1, ni = n - 1;
+  const int64_t V = nverts(n);
+  const int nI = ni * ni * ni, m = 3 * nI;
+  const double* xcm = tk.m1;
+  const double* xrm = tk.m2;
+  const T* r = static_cast<const T*>(tk.src);
+  T* z = static_cast<T*>(tk.dst);
+  double* rs = sm;
+  double* ts = sm + m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    const int c = q / nI, iv = q % nI;
+    const int i = 1 + iv % ni, j = 1 + (iv / ni) % ni, k = 1 + iv / (ni * ni);
+    rs[q] = (double)r[c * V + i + (int64_t)nv * (j + (int64_t)nv * k)];
+  }
+  __syncthreads();
+  for (int q = warp; q < m; q += nw) {
+    double s = 0.0;
+    for (int p = lane; p <= q; p += 32) s = fma(xrm[(int64_t)q * m + p], rs[p], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) ts[q] = s;
+  }
+  __syncthreads();
+  for (int q = warp; q < m; q += nw) {
+    double s = 0.0;
+    for (int p = q + lane; p < m; p += 32) s = fma(xcm[(int64_t)q * m + p], ts[p], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) rs[q] = s;
+  }
+  __syncthreads();
+  for (int64_t id = threadIdx.x; id < 3 * V; id += blockDim.x) {
+    const int c = (int)(id / V);
+    const int64_t v = id % V;
+    const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
+    T out = T(0);
+    if (inner) out = (T)rs[c * nI + (i - 1) + ni * ((j - 1) + ni * (k - 1))];
+    z[id] = out;
+  }
+}
+
+// ------------------------------------------------------------------ Krylov
+template <int OP>
+__global__ void __launch_bounds__(kBT) reduce_batch_kernel(const KTask* __restrict__ tasks, double* partials) {
+  const KTask tk = tasks[blockIdx.y];
+  double acc = 0.0;
+  if (!skip(tk.sc)) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tk.n; i += (int64_t)gridDim.x * blockDim.x)
+      acc = (OP == KB_DOT) ? fma(tk.a[i], tk.b[i], acc) : acc + tk.a[i];
+  }
+  __shared__ double red[kBT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kBT / 32; ++w) v += red[w];
+    partials[blockIdx.y * kDotBlocks + blockIdx.x] = v;
+  }
+}
+
+__global__ void reduce_batch_final_kernel(const KTask* __restrict__ tasks, const double* partials) {
+  const KTask tk = tasks[blockIdx.x];
+  if (skip(tk.sc)) return;
+  __shared__ double red[kDotBlocks];
+  red[threadIdx.x] = partials[blockIdx.x * kDotBlocks + threadIdx.x];
+  __syncthreads();
+  for (int s = kDotBlocks / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tk.sc[tk.slot] = tk.scale * red[0];
+}
+
+__global__ void vec_batch_kernel(const KTask* __restrict__ tasks, int op) {
+  const KTask tk = tasks[blockIdx.y];
+  if (op == KB_UPDATE ? tk.sc[MS_UPD_SKIP] != 0.0 : skip(tk.sc)) return;
+  const double* sc = tk.sc;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  if (op == KB_LANCZOS) {  // c <- a/g - (delta/g) b - (g/g_old) c   (a = Kz, b = v, c = v_old)
+    const double g = sc[MS_GAMMA], go = sc[MS_GAMMA_OLD];
+    const double ig = 1.0 / g;
+    const double delta = sc[MS_DOT_KZZ] * ig * ig;
+    const double al = delta * ig, be = g / go;
+    for (int64_t i = i0; i < tk.n; i += st) tk.c[i] = tk.a[i] * ig - al * tk.b[i] - be * tk.c[i];
+  } else if (op == KB_UPDATE) {  // c <- (a/g_prev - a3 c - a2 b)/a1 ; d += xcoef c   (a = z, b = w, c = w_old, d = x)
+    const double ig = sc[MS_INV_GAMMA_PREV], a1 = sc[MS_A1], a2 = sc[MS_A2], a3 = sc[MS_A3], xc = sc[MS_XCOEF];
+    const double ia1 = 1.0 / a1;
+    for (int64_t i = i0; i < tk.n; i += st) {
+      const double wn = (tk.a[i] * ig - a3 * tk.c[i] - a2 * tk.b[i]) * ia1;
+      tk.c[i] = wn;
+      tk.d[i] = fma(xc, wn, tk.d[i]);
+    }
+  } else if (op == KB_PDIV) {  // c <- (a - sc[slot]) * b
+    const double m = sc[tk.slot];
+    for (int64_t i = i0; i < tk.n; i += st) tk.c[i] = (tk.a[i] - m) * tk.b[i];
+  } else if (op == KB_SUBS) {  // c <- a - sc[slot]
+    const double m = sc[tk.slot];
+    for (int64_t i = i0; i < tk.n; i += st) tk.c[i] = tk.a[i] - m;
+  }
+}
+
+// MINRES scalar recurrence, one thread per problem (as minres_scalar_kernel)
+__device__ void scalars_one(double* sc) {
+  if (sc[MS_DONE] != 0.0) {
+    sc[MS_UPD_SKIP] = 1.0;
+    return;
+  }
+  const double g = sc[MS_GAMMA];
+  const double delta = sc[MS_DOT_KZZ] / (g * g);
+  const double gn2 = sc[MS_DOT_ZV];
+  const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
+  const double c = sc[MS_C], co = sc[MS_C_OLD], s = sc[MS_S], so = sc[MS_S_OLD];
+  const double a0 = c * delta - co * s * g;
+  const double a1 = sqrt(a0 * a0 + gn * gn);
+  const double a2 = s * delta + co * c * g;
+  const double a3 = so * g;
+  const double eta = sc[MS_ETA];
+  if (!(a1 > 0.0) || !isfinite(a1)) {
+    sc[MS_DONE] = 2.0;
+    sc[MS_UPD_SKIP] = 1.0;
+    return;
+  }
+  const double cn = a0 / a1, sn = gn / a1;
+  sc[MS_A1] = a1;
+  sc[MS_A2] = a2;
+  sc[MS_A3] = a3;
+  sc[MS_XCOEF] = cn * eta;
+  sc[MS_INV_GAMMA_PREV] = 1.0 / g;
+  sc[MS_UPD_SKIP] = 0.0;
+  sc[MS_ETA] = -sn * eta;
+  sc[MS_C_OLD] = c;
+  sc[MS_C] = cn;
+  sc[MS_S_OLD] = s;
+  sc[MS_S] = sn;
+  sc[MS_GAMMA_OLD] = g;
+  sc[MS_GAMMA] = gn;
+  sc[MS_ITERS] += 1.0;
+  if (fabs(sc[MS_ETA]) <= sc[MS_TOL_ABS] || !(gn > 0.0)) sc[MS_DONE] = 1.0;
+}
+
+__global__ void scalars_batch_kernel(const KTask* __restrict__ tasks, int ntasks) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ntasks) return;
+  double* sc = tasks[p].sc;
+  scalars_one(sc);
+  if (tasks[p].c) tasks[p].c[0] = sc[MS_DONE];  // contiguous copy of the done flags for the host
+}
+
+
+inline unsigned chunks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_xfer_batch(int kind, const XferTask* tasks, int ntasks, int64_t max_count, int max_m,
+                              cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  dim3 g(chunks(max_count, kBT), (unsigned)ntasks);
+  switch (kind) {
+    case XK_RESTRICT: restrict_batch_kernel<T><<<g, kBT, 0, s>>>(tasks); break;
+    case XK_PROLONG_ADD: prolong_batch_kernel<T, true><<<g, kBT, 0, s>>>(tasks); break;
+    case XK_PROLONG: prolong_batch_kernel<T, false><<<g, kBT, 0, s>>>(tasks); break;
+    case XK_COPY64: convert_batch_kernel<double, double><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
+    case XK_D2F: convert_batch_kernel<double, float><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
+    case XK_F2D: convert_batch_kernel<float, double><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
+    case XK_COARSE:
+      coarse_solve_batch_kernel<T><<<ntasks, 1024, 2 * (size_t)max_m * sizeof(double), s>>>(tasks);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_xfer_batch<float>(int, const XferTask*, int, int64_t, int, cudaStream_t);
+template cudaError_t launch_xfer_batch<double>(int, const XferTask*, int, int64_t, int, cudaStream_t);
+
+cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t max_n, double* partials,
+                                cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  switch (op) {
+    case KB_DOT:
+      reduce_batch_kernel<KB_DOT><<<dim3(kDotBlocks, ntasks), kBT, 0, s>>>(tasks, partials);
+      reduce_batch_final_kernel<<<ntasks, kDotBlocks, 0, s>>>(tasks, partials);
+      break;
+    case KB_SUM:
+      reduce_batch_kernel<KB_SUM><<<dim3(kDotBlocks, ntasks), kBT, 0, s>>>(tasks, partials);
+      reduce_batch_final_kernel<<<ntasks, kDotBlocks, 0, s>>>(tasks, partials);
+      break;
+    case KB_SCALARS: scalars_batch_kernel<<<chunks(ntasks, 32), 32, 0, s>>>(tasks, ntasks); break;
+    default: {
+      dim3 g(std::min<unsigned>(chunks(max_n, kBT), 1216u), (unsigned)ntasks);
+      vec_batch_kernel<<<g, kBT, 0, s>>>(tasks, op);
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace agca

@@ -4,6 +4,11 @@
 #include <math.h>
 
 #include <algorithm>
+#include <array>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -55,7 +60,7 @@ struct agca_ctx {
   int N = 0, L = 0, prec = 0;
   cudaStream_t stream = nullptr;
   int cheb_degree = 2;
-  double cheb_lo = 0.3, cheb_hi = 1.2;
+  double cheb_lo = 0.1, cheb_hi = 1.1;
   int power_iters = 20;
   std::vector<Level> lev;  // 1..L
   // workspace
@@ -83,6 +88,8 @@ struct agca_ctx {
   // kernel launches issued by this context, and optional per-launch timing
   // of the finest-level stencil kernels (agca_profile_fine)
   int64_t launches = 0;
+  // tile shape per level and stencil mode (autotuner; default by = 8, automatic z-chunk)
+  std::vector<std::array<TileCfg, 6>> tune;
   // V-cycles replayed from CUDA graphs, keyed by their (input, output) pointers
   struct GraphEntry {
     const void* r;
@@ -309,7 +316,8 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
   a.s2 = (T)s2;
   const bool timed = ctx->prof && l == ctx->L && ctx->ev_used + 2 <= ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
-  LK((l < ctx->L && lv.n_flag > 0) ? 2 : 1, launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream));
+  const TileCfg* cfg = (mode >= 0 && mode < 6) ? &ctx->tune[l][mode] : nullptr;
+  LK((l < ctx->L && lv.n_flag > 0) ? 2 : 1, launch_stencil<T, T>(mode, level_op<T>(ctx, l), a, ctx->stream, cfg));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
     ctx->ev_used += 2;
@@ -623,7 +631,467 @@ agca_status power_lambda(agca_ctx* ctx, int l, double* lam) {
 
 bool valid_level(const agca_ctx* ctx, int l) { return l >= 1 && l <= ctx->L; }
 
+// Autotuner: times every candidate tile shape (block rows, z-chunk) of the
+// V-cycle stencil launches on each level with CUDA events on the context
+// stream and keeps the fastest; results can be cached in a text file keyed
+// by (precision, cubes per axis, mode, coarse).
+template <typename T>
+agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, TileCfg>& cache) {
+  Level& lv = ctx->lev[l];
+  const int64_t n3 = 3 * lv.V;
+  cudaStream_t s = ctx->stream;
+  for (void* p : {lv.vb, lv.vx, lv.vt, lv.vr}) CK(cudaMemsetAsync(p, 0, n3 * sizeof(T), s));
+  const bool f32 = sizeof(T) == 4;
+  std::vector<int> bys = f32 ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
+  const int nv = lv.n + 1;
+  std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int modes[4] = {ST_CHEB_PRE, ST_RESID, ST_CHEB_FIRST, ST_CHEB_STEP};
+  agca_status st = AGCA_OK;
+  for (int mode : modes) {
+    std::ostringstream key;
+    key << (f32 ? "f32" : "f64") << ' ' << lv.n << ' ' << mode << ' ' << (l < ctx->L ? 1 : 0);
+    auto it = cache.find(key.str());
+    if (it != cache.end()) {
+      ctx->tune[l][mode] = it->second;
+      continue;
+    }
+    TileCfg best;
+    float best_ms = 1e30f;
+    for (int by : bys) {
+      int last_zch = -1;
+      for (int zr : zs) {
+        if (zr > nv) continue;
+        int gx, gy, gz, zch;
+        stencil_grid_by(lv.n, by, zr, &gx, &gy, &gz, &zch);
+        if (zch == last_zch) continue;
+        last_zch = zch;
+        TileCfg c;
+        c.by = by;
+        c.zch = zch;
+        ctx->tune[l][mode] = c;
+        T* X = static_cast<T*>(lv.vx);
+        T* Bv = static_cast<T*>(lv.vb);
+        T* Tb = static_cast<T*>(lv.vt);
+        T* R = static_cast<T*>(lv.vr);
+        auto once = [&]() -> agca_status {
+          switch (mode) {
+            case ST_CHEB_PRE: return stencil<T>(ctx, mode, l, nullptr, Bv, nullptr, X, 0.5, 0.5, 0.5);
+            case ST_RESID: return stencil<T>(ctx, mode, l, X, Bv, nullptr, R, 0, 0, 0);
+            case ST_CHEB_FIRST: return stencil<T>(ctx, mode, l, X, Bv, nullptr, Tb, 0.5, 0, 0);
+            default: return stencil<T>(ctx, mode, l, Tb, Bv, X, X, 0.5, 0.5, 0);
+          }
+        };
+        if ((st = once()) != AGCA_OK) break;
+        if ((st = once()) != AGCA_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) break;
+        for (int r = 0; r < reps && st == AGCA_OK; ++r) st = once();
+        if (st != AGCA_OK) break;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+      if (st != AGCA_OK) break;
+    }
+    if (st != AGCA_OK) break;
+    ctx->tune[l][mode] = best;
+    cache[key.str()] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+// ===================================================================== batch
+// Many independent problems solved together: every problem has its own
+// context (hierarchy, workspace slice, MINRES state); the MINRES iteration of
+// all problems runs in lockstep as one CUDA graph whose launches each cover
+// every problem (persistent stencil launches over the (problem, tile) work
+// list, 2-D element-wise grids over (chunk, problem)), skipping converged
+// problems on the device.
+struct BatchStep {
+  int kind;        // 0 stencil, 1 xfer, 2 krylov
+  int mode;        // stencil mode / xfer kind / krylov op
+  int prec;        // 0: <double,double>, 1: <float,float>, 2: <double,float>
+  bool coarse;
+  size_t off;      // byte offset of the task array in the task table
+  int ntasks;
+  int64_t work;    // tiles (stencil), max count (xfer), max n (krylov)
+  int64_t gca;     // max gca rows (coarse stencil)
+  int max_m;       // coarsest solve size
+};
+
 }  // namespace
+
+struct agca_batch {
+  int n = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<agca_ctx*> ctx;
+  std::vector<size_t> ws_off, gs_off;
+  size_t ws_need = 0, gs_need = 0, tab_bytes = 0;
+  char* ws = nullptr;
+  char* gs = nullptr;
+  char* tab = nullptr;       // device task tables
+  double* partials = nullptr;
+  std::vector<char> host_tab;
+  std::vector<BatchStep> iter_steps[2];  // MINRES iteration, by buffer parity
+  cudaGraphExec_t iter_graph = nullptr;
+  int64_t iter_launches = 0;
+  bool setup_done = false;
+  std::string err;
+  agca_status fail(agca_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  ~agca_batch() {
+    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    for (agca_ctx* c : ctx) delete c;
+  }
+};
+
+#define BCK(...)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (__VA_ARGS__);                                                                  \
+    if (e_ != cudaSuccess)                                                                           \
+      return b->fail(AGCA_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+#define BCKS(expr)                                                                                   \
+  do {                                                                                               \
+    agca_status s_ = (expr);                                                                         \
+    if (s_ != AGCA_OK) return s_;                                                                    \
+  } while (0)
+
+namespace {
+
+template <typename TaskT>
+size_t push_tasks(agca_batch* b, const std::vector<TaskT>& t) {
+  size_t off = (b->host_tab.size() + 255) / 256 * 256;
+  b->host_tab.resize(off + t.size() * sizeof(TaskT));
+  if (!t.empty()) std::memcpy(b->host_tab.data() + off, t.data(), t.size() * sizeof(TaskT));
+  return off;
+}
+
+template <typename TS, typename T>
+StencilTask<TS, T> make_task(agca_ctx* c, int l, int mode, const TS* x, const TS* bb, const TS* xprev, TS* out,
+                             double s0, double s1, double s2, const double* sc) {
+  StencilTask<TS, T> tk{};
+  tk.op = level_op<T>(c, l);
+  tk.a.x = x;
+  tk.a.b = bb;
+  tk.a.invD = (const TS*)invD_of<T>(c->lev[l]);
+  tk.a.xprev = xprev;
+  tk.a.out = out;
+  tk.a.s0 = (TS)s0;
+  tk.a.s1 = (TS)s1;
+  tk.a.s2 = (TS)s2;
+  stencil_grid(c->lev[l].n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
+  tk.sc = sc;
+  (void)mode;
+  return tk;
+}
+
+template <typename TS, typename T>
+void push_stencil(agca_batch* b, std::vector<BatchStep>& steps, int mode, bool coarse, std::vector<StencilTask<TS, T>> t,
+                  int prec) {
+  if (t.empty()) return;
+  int64_t tiles = 0, gca = 0;
+  for (auto& tk : t) {
+    tk.tile0 = tiles;
+    tiles += (int64_t)tk.gx * tk.gy * tk.gz;
+    gca = std::max<int64_t>(gca, tk.op.n_flag * 12);
+  }
+  BatchStep st{0, mode, prec, coarse, push_tasks(b, t), (int)t.size(), tiles, coarse ? gca : 0, 0};
+  steps.push_back(st);
+}
+
+void push_xfer(agca_batch* b, std::vector<BatchStep>& steps, int kind, const std::vector<XferTask>& t, int prec) {
+  if (t.empty()) return;
+  int64_t mx = 0;
+  int mm = 0;
+  for (auto& tk : t) {
+    mx = std::max(mx, tk.count);
+    if (kind == XK_COARSE) mm = std::max(mm, 3 * (tk.nf - 1) * (tk.nf - 1) * (tk.nf - 1));
+  }
+  BatchStep st{1, kind, prec, false, push_tasks(b, t), (int)t.size(), mx, 0, mm};
+  steps.push_back(st);
+}
+
+void push_krylov(agca_batch* b, std::vector<BatchStep>& steps, int op, const std::vector<KTask>& t) {
+  if (t.empty()) return;
+  int64_t mx = 0;
+  for (auto& tk : t) mx = std::max(mx, tk.n);
+  BatchStep st{2, op, 0, false, push_tasks(b, t), (int)t.size(), mx, 0, 0};
+  steps.push_back(st);
+}
+
+// Batched V(2,2) cycle z_p = V_p(r_p) (degree-2 Chebyshev), result copied to z_p.
+template <typename T>
+void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector<const double*>& r,
+                 const std::vector<double*>& z, bool skip_done) {
+  const int P = b->n;
+  const int pr = std::is_same<T, float>::value ? 1 : 0;
+  const bool mixed = std::is_same<T, float>::value;
+  int maxL = 0;
+  for (auto* c : b->ctx) maxL = std::max(maxL, c->L);
+  auto sc_of = [&](int p) -> const double* { return skip_done ? b->ctx[p]->sc : nullptr; };
+  auto bfine = [&](int p) -> const T* {
+    agca_ctx* c = b->ctx[p];
+    return mixed ? static_cast<const T*>(c->lev[c->L].vb) : reinterpret_cast<const T*>(r[p]);
+  };
+  if (mixed) {
+    std::vector<XferTask> t;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* c = b->ctx[p];
+      XferTask x{};
+      x.count = 3 * c->lev[c->L].V;
+      x.src = r[p];
+      x.dst = c->lev[c->L].vb;
+      x.sc = sc_of(p);
+      t.push_back(x);
+    }
+    push_xfer(b, steps, XK_D2F, t, 1);
+  }
+  // down-sweep by depth below each problem's finest level
+  for (int d = 0; d <= maxL - 2; ++d) {
+    std::vector<StencilTask<T, T>> pre, res;
+    std::vector<XferTask> rst;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* c = b->ctx[p];
+      const int l = c->L - d;
+      if (l < 2) continue;
+      Level& lv = c->lev[l];
+      const T* bl = (d == 0) ? bfine(p) : static_cast<const T*>(lv.vb);
+      T* X = static_cast<T*>(lv.vx);
+      const Cheb ch = cheb_params(c, l);
+      const double rho = 1.0 / ch.sigma, rn = 1.0 / (2.0 * ch.sigma - rho);
+      pre.push_back(make_task<T, T>(c, l, ST_CHEB_PRE, nullptr, bl, nullptr, X, rn * rho, 2.0 * rn / ch.delta,
+                                    1.0 / ch.theta, sc_of(p)));
+      res.push_back(make_task<T, T>(c, l, ST_RESID, X, bl, nullptr, static_cast<T*>(lv.vr), 0, 0, 0, sc_of(p)));
+      XferTask x{};
+      x.nf = lv.n;
+      x.ncomp = 3;
+      x.mask = 1;
+      x.scale = 1.0;
+      x.count = c->lev[l - 1].V;
+      x.src = lv.vr;
+      x.dst = c->lev[l - 1].vb;
+      x.sc = sc_of(p);
+      rst.push_back(x);
+    }
+    push_stencil<T, T>(b, steps, ST_CHEB_PRE, d > 0, pre, pr);
+    push_stencil<T, T>(b, steps, ST_RESID, d > 0, res, pr);
+    push_xfer(b, steps, XK_RESTRICT, rst, pr);
+  }
+  {
+    std::vector<XferTask> t;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* c = b->ctx[p];
+      XferTask x{};
+      x.nf = c->lev[1].n;
+      x.count = 1;
+      x.src = c->lev[1].vb;
+      x.dst = c->lev[1].vx;
+      x.m1 = c->linv_cm;
+      x.m2 = c->linv_rm;
+      x.sc = sc_of(p);
+      t.push_back(x);
+    }
+    push_xfer(b, steps, XK_COARSE, t, pr);
+  }
+  for (int d = maxL - 2; d >= 0; --d) {
+    std::vector<StencilTask<T, T>> first, step;
+    std::vector<XferTask> pro;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* c = b->ctx[p];
+      const int l = c->L - d;
+      if (l < 2) continue;
+      Level& lv = c->lev[l];
+      const T* bl = (d == 0) ? bfine(p) : static_cast<const T*>(lv.vb);
+      T* X = static_cast<T*>(lv.vx);
+      T* Tb = static_cast<T*>(lv.vt);
+      XferTask x{};
+      x.nf = lv.n;
+      x.ncomp = 3;
+      x.mask = 1;
+      x.count = lv.V;
+      x.src = c->lev[l - 1].vx;
+      x.dst = X;
+      x.sc = sc_of(p);
+      pro.push_back(x);
+      const Cheb ch = cheb_params(c, l);
+      const double rho = 1.0 / ch.sigma, rn = 1.0 / (2.0 * ch.sigma - rho);
+      first.push_back(make_task<T, T>(c, l, ST_CHEB_FIRST, X, bl, nullptr, Tb, 1.0 / ch.theta, 0, 0, sc_of(p)));
+      step.push_back(make_task<T, T>(c, l, ST_CHEB_STEP, Tb, bl, X, X, rn * rho, 2.0 * rn / ch.delta, 0, sc_of(p)));
+    }
+    push_xfer(b, steps, XK_PROLONG_ADD, pro, pr);
+    push_stencil<T, T>(b, steps, ST_CHEB_FIRST, d > 0, first, pr);
+    push_stencil<T, T>(b, steps, ST_CHEB_STEP, d > 0, step, pr);
+  }
+  {
+    std::vector<XferTask> t;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* c = b->ctx[p];
+      XferTask x{};
+      x.count = 3 * c->lev[c->L].V;
+      x.src = c->lev[c->L].vx;
+      x.dst = z[p];
+      x.sc = sc_of(p);
+      t.push_back(x);
+    }
+    push_xfer(b, steps, mixed ? XK_F2D : XK_COPY64, t, pr);
+  }
+}
+
+// K x for every problem (x_p, y_p: Stokes vectors), FP32 compute when low
+void build_stokes(agca_batch* b, std::vector<BatchStep>& steps, const std::vector<const double*>& x,
+                  const std::vector<double*>& y, bool low, bool skip_done) {
+  const int P = b->n;
+  std::vector<XferTask> pro, rst;
+  std::vector<StencilTask<double, double>> t64;
+  std::vector<StencilTask<double, float>> t32;
+  for (int p = 0; p < P; ++p) {
+    agca_ctx* c = b->ctx[p];
+    const Level& lf = c->lev[c->L];
+    const int64_t n3 = 3 * lf.V;
+    const double* sc = skip_done ? c->sc : nullptr;
+    XferTask a{};
+    a.nf = lf.n;
+    a.ncomp = 1;
+    a.mask = 0;
+    a.count = lf.V;
+    a.src = x[p] + n3;
+    a.dst = c->qfine;
+    a.sc = sc;
+    pro.push_back(a);
+    if (low) {
+      StencilTask<double, float> tk{};
+      tk.op = op32(c, c->L);
+      tk.a.x = x[p];
+      tk.a.q = c->qfine;
+      tk.a.out = y[p];
+      tk.a.out2 = c->sfine;
+      stencil_grid(lf.n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
+      tk.sc = sc;
+      t32.push_back(tk);
+    } else {
+      StencilTask<double, double> tk{};
+      tk.op = op64(c, c->L);
+      tk.a.x = x[p];
+      tk.a.q = c->qfine;
+      tk.a.out = y[p];
+      tk.a.out2 = c->sfine;
+      stencil_grid(lf.n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
+      tk.sc = sc;
+      t64.push_back(tk);
+    }
+    XferTask r{};
+    r.nf = lf.n;
+    r.ncomp = 1;
+    r.mask = 0;
+    r.scale = -1.0;
+    r.count = c->Vp;
+    r.src = c->sfine;
+    r.dst = y[p] + n3;
+    r.sc = sc;
+    rst.push_back(r);
+  }
+  push_xfer(b, steps, XK_PROLONG, pro, 0);
+  if (low)
+    push_stencil<double, float>(b, steps, ST_STOKES, false, t32, 2);
+  else
+    push_stencil<double, double>(b, steps, ST_STOKES, false, t64, 0);
+  push_xfer(b, steps, XK_RESTRICT, rst, 0);
+}
+
+// One MINRES iteration for every problem at buffer parity par (see minres_impl).
+void build_iteration(agca_batch* b, int par) {
+  std::vector<BatchStep>& steps = b->iter_steps[par];
+  steps.clear();
+  const int P = b->n;
+  const bool mixed = b->prec == AGCA_MIXED;
+  std::vector<const double*> z(P), vnew_c(P);
+  std::vector<double*> kz(P), vnew(P), zn(P);
+  for (int p = 0; p < P; ++p) {
+    agca_ctx* c = b->ctx[p];
+    z[p] = c->kv[par ? KV_ZNEW : KV_Z];
+    zn[p] = c->kv[par ? KV_Z : KV_ZNEW];
+    kz[p] = c->kv[KV_KZ];
+    vnew[p] = c->kv[par ? KV_V : KV_VOLD];
+    vnew_c[p] = vnew[p];
+  }
+  build_stokes(b, steps, z, kz, mixed, true);
+  std::vector<KTask> dk, lz, pz, ps, pd, pm, dz, up, sc;
+  for (int p = 0; p < P; ++p) {
+    agca_ctx* c = b->ctx[p];
+    const int64_t nt = c->nt, n3 = nt - c->Vp;
+    const double* v = c->kv[par ? KV_VOLD : KV_V];
+    const double* w = c->kv[par ? KV_WOLD : KV_W];
+    double* wold = c->kv[par ? KV_W : KV_WOLD];
+    dk.push_back({nt, c->sc, kz[p], z[p], nullptr, nullptr, MS_DOT_KZZ, 1.0});
+    lz.push_back({nt, c->sc, kz[p], v, vnew[p], nullptr, 0, 0.0});
+    ps.push_back({c->Vp, c->sc, vnew[p] + n3, nullptr, nullptr, nullptr, MS_TMP0, 1.0 / (double)c->Vp});
+    pd.push_back({c->Vp, c->sc, vnew[p] + n3, c->pmass_inv, zn[p] + n3, nullptr, MS_TMP0, 0.0});
+    pm.push_back({c->Vp, c->sc, zn[p] + n3, nullptr, nullptr, nullptr, MS_TMP1, 1.0 / (double)c->Vp});
+    pz.push_back({c->Vp, c->sc, zn[p] + n3, nullptr, zn[p] + n3, nullptr, MS_TMP1, 0.0});
+    dz.push_back({nt, c->sc, zn[p], vnew[p], nullptr, nullptr, MS_DOT_ZV, 1.0});
+    sc.push_back({0, c->sc, nullptr, nullptr, nullptr, nullptr, 0, 0.0});
+    up.push_back({nt, c->sc, z[p], w, wold, c->kv[KV_D], 0, 0.0});
+  }
+  push_krylov(b, steps, KB_DOT, dk);
+  push_krylov(b, steps, KB_LANCZOS, lz);
+  if (mixed)
+    build_cycle<float>(b, steps, vnew_c, zn, true);
+  else
+    build_cycle<double>(b, steps, vnew_c, zn, true);
+  push_krylov(b, steps, KB_SUM, ps);
+  push_krylov(b, steps, KB_PDIV, pd);
+  push_krylov(b, steps, KB_SUM, pm);
+  push_krylov(b, steps, KB_SUBS, pz);
+  push_krylov(b, steps, KB_DOT, dz);
+  push_krylov(b, steps, KB_SCALARS, sc);
+  push_krylov(b, steps, KB_UPDATE, up);
+}
+
+agca_status run_steps(agca_batch* b, const std::vector<BatchStep>& steps, int64_t* launches) {
+  cudaStream_t s = b->stream;
+  for (const BatchStep& st : steps) {
+    const void* t = b->tab + st.off;
+    if (st.kind == 0) {
+      if (st.prec == 0)
+        BCK(launch_stencil_batch<double, double>(st.mode, st.coarse, (const StencilTask<double, double>*)t, st.ntasks,
+                                                 st.work, st.gca, s));
+      else if (st.prec == 1)
+        BCK(launch_stencil_batch<float, float>(st.mode, st.coarse, (const StencilTask<float, float>*)t, st.ntasks,
+                                               st.work, st.gca, s));
+      else
+        BCK(launch_stencil_batch<double, float>(st.mode, st.coarse, (const StencilTask<double, float>*)t, st.ntasks,
+                                                st.work, st.gca, s));
+      *launches += (st.coarse && st.gca > 0) ? 2 : 1;
+    } else if (st.kind == 1) {
+      if (st.prec == 1)
+        BCK(launch_xfer_batch<float>(st.mode, (const XferTask*)t, st.ntasks, st.work, st.max_m, s));
+      else
+        BCK(launch_xfer_batch<double>(st.mode, (const XferTask*)t, st.ntasks, st.work, st.max_m, s));
+      *launches += 1;
+    } else {
+      BCK(launch_krylov_batch(st.mode, (const KTask*)t, st.ntasks, st.work, b->partials, s));
+      *launches += (st.mode == KB_DOT || st.mode == KB_SUM) ? 2 : 1;
+    }
+  }
+  return AGCA_OK;
+}
+
+bool batch_valid(const agca_batch* b, int i) { return b && i >= 0 && i < b->n; }
+
+}  // namespace
+
 
 extern "C" {
 
@@ -668,6 +1136,7 @@ agca_status agca_create(int N, int n_levels, int prec, void* cuda_stream, agca_c
   }
   ctx->Vp = nverts(nL / 2);
   ctx->nt = 3 * ctx->lev[n_levels].V + ctx->Vp;
+  ctx->tune.assign(n_levels + 1, std::array<TileCfg, 6>{});
   carve_workspace(ctx, nullptr);
   *out = ctx;
   return AGCA_OK;
@@ -908,6 +1377,45 @@ agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const doub
   return AGCA_OK;
 }
 
+agca_status agca_autotune(agca_ctx* ctx, int reps, const char* cache_path) {
+  if (!ctx) return AGCA_EINVAL;
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  if (reps < 1 || reps > 10000) return ctx->fail(AGCA_EINVAL, "reps out of range");
+  ctx->clear_graphs();
+  std::map<std::string, TileCfg> cache;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string pr;
+    int n, mode, coarse, by, zch;
+    while (in >> pr >> n >> mode >> coarse >> by >> zch) {
+      std::ostringstream key;
+      key << pr << ' ' << n << ' ' << mode << ' ' << coarse;
+      TileCfg c;
+      c.by = by;
+      c.zch = zch;
+      cache[key.str()] = c;
+    }
+  }
+  for (int l = 2; l <= ctx->L; ++l) {
+    const agca_status st = ctx->prec == AGCA_MIXED ? tune_level<float>(ctx, l, reps, cache)
+                                                   : tune_level<double>(ctx, l, reps, cache);
+    if (st != AGCA_OK) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (cache_path) {
+    std::ofstream out(cache_path);
+    for (auto& kv : cache) out << kv.first << ' ' << kv.second.by << ' ' << kv.second.zch << '\n';
+  }
+  return AGCA_OK;
+}
+
+agca_status agca_tile_config(const agca_ctx* ctx, int level, int mode, int* by, int* zch) {
+  if (!ctx || !by || !zch || level < 1 || level > ctx->L || mode < 0 || mode > 5) return AGCA_EINVAL;
+  *by = ctx->tune[level][mode].by;
+  *zch = ctx->tune[level][mode].zch;
+  return AGCA_OK;
+}
+
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches) {
   if (!ctx || !launches) return AGCA_EINVAL;
   *launches = ctx->launches;
@@ -990,5 +1498,300 @@ agca_status agca_get_level_data(agca_ctx* ctx, int level, int field, void* dst_d
   if (bytes) CK(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   return AGCA_OK;
 }
+
+// ============================================================== batch C ABI
+static int default_levels_for(int N) {
+  int n = 2 * N, L = 1;
+  while (n % 2 == 0 && n / 2 >= 4) {
+    n /= 2;
+    ++L;
+  }
+  return L;
+}
+
+agca_status agca_batch_create(int n, const int* Ns, int prec, void* cuda_stream, agca_batch** out) {
+  if (!out || !Ns || n < 1 || n > 4096) return AGCA_EINVAL;
+  *out = nullptr;
+  agca_batch* b = new agca_batch();
+  b->n = n;
+  b->prec = prec;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  size_t off = 0;
+  size_t max_task = std::max(sizeof(StencilTask<double, double>), std::max(sizeof(XferTask), sizeof(KTask)));
+  for (int i = 0; i < n; ++i) {
+    agca_ctx* c = nullptr;
+    const agca_status st = agca_create(Ns[i], default_levels_for(Ns[i]), prec, cuda_stream, &c);
+    if (st != AGCA_OK) {
+      delete b;
+      return st;
+    }
+    b->ctx.push_back(c);
+    b->ws_off.push_back(off);
+    off += (c->ws_need + kAlign - 1) / kAlign * kAlign;
+  }
+  // task tables: two MINRES iteration parities plus one per-call V-cycle set,
+  // at most ~8 steps per level and 24 fixed steps, one task per problem each
+  int maxL = 0;
+  for (auto* c : b->ctx) maxL = std::max(maxL, c->L);
+  const size_t steps = (size_t)8 * maxL + 32;
+  b->tab_bytes = 3 * steps * ((size_t)n * max_task + 256) + (1 << 16);
+  b->ws_off.push_back(off);  // table
+  off += (b->tab_bytes + kAlign - 1) / kAlign * kAlign;
+  b->ws_off.push_back(off);  // reduction partials and done flags
+  off += ((size_t)n * 64 + n) * sizeof(double);
+  b->ws_need = (off + kAlign - 1) / kAlign * kAlign;
+  *out = b;
+  return AGCA_OK;
+}
+
+void agca_batch_destroy(agca_batch* b) { delete b; }
+
+const char* agca_batch_last_error(const agca_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+agca_status agca_batch_workspace_size(const agca_batch* b, size_t* bytes) {
+  if (!b || !bytes) return AGCA_EINVAL;
+  *bytes = b->ws_need;
+  return AGCA_OK;
+}
+
+agca_status agca_batch_bind_workspace(agca_batch* b, void* dev_ptr, size_t bytes) {
+  if (!b) return AGCA_EINVAL;
+  if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return b->fail(AGCA_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < b->ws_need) return b->fail(AGCA_ENOMEM, "workspace too small");
+  b->ws = static_cast<char*>(dev_ptr);
+  for (int i = 0; i < b->n; ++i) {
+    const agca_status st = agca_bind_workspace(b->ctx[i], b->ws + b->ws_off[i], b->ctx[i]->ws_need);
+    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
+  }
+  b->tab = b->ws + b->ws_off[b->n];
+  b->partials = reinterpret_cast<double*>(b->ws + b->ws_off[b->n + 1]);
+  b->setup_done = false;
+  return AGCA_OK;
+}
+
+agca_status agca_batch_set_viscosity(agca_batch* b, int i, const double* eta_dev) {
+  if (!batch_valid(b, i) || !eta_dev) return AGCA_EINVAL;
+  b->setup_done = false;
+  const agca_status st = agca_set_viscosity(b->ctx[i], eta_dev);
+  return st == AGCA_OK ? st : b->fail(st, b->ctx[i]->err);
+}
+
+agca_status agca_batch_flag(agca_batch* b, double nu, size_t* gca_bytes) {
+  if (!b || !gca_bytes) return AGCA_EINVAL;
+  b->gs_off.assign(b->n + 1, 0);
+  size_t off = 0;
+  for (int i = 0; i < b->n; ++i) {
+    size_t g = 0;
+    const agca_status st = agca_flag(b->ctx[i], nu, &g);
+    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
+    b->gs_off[i] = off;
+    off += (g + kAlign - 1) / kAlign * kAlign;
+  }
+  b->gs_off[b->n] = off;
+  b->gs_need = off;
+  *gca_bytes = off;
+  b->setup_done = false;
+  return AGCA_OK;
+}
+
+agca_status agca_batch_bind_gca_store(agca_batch* b, void* dev_ptr, size_t bytes) {
+  if (!b) return AGCA_EINVAL;
+  if (b->gs_off.empty()) return b->fail(AGCA_ESTATE, "flag first");
+  if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign) != 0) return b->fail(AGCA_EINVAL, "store must be 256-byte aligned");
+  if (bytes < b->gs_need) return b->fail(AGCA_ENOMEM, "Galerkin store too small");
+  b->gs = static_cast<char*>(dev_ptr);
+  for (int i = 0; i < b->n; ++i) {
+    const agca_status st = agca_bind_gca_store(b->ctx[i], b->gs + b->gs_off[i], b->ctx[i]->gs_need);
+    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
+  }
+  return AGCA_OK;
+}
+
+agca_status agca_batch_setup(agca_batch* b) {
+  if (!b) return AGCA_EINVAL;
+  if (!b->ws || !b->gs) return b->fail(AGCA_ESTATE, "bind the workspace and the Galerkin store first");
+  for (int i = 0; i < b->n; ++i) {
+    const agca_status st = agca_setup(b->ctx[i]);
+    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
+  }
+  // task tables of the lockstep MINRES iteration (both buffer parities)
+  b->host_tab.clear();
+  build_iteration(b, 0);
+  build_iteration(b, 1);
+  // publish every problem's done flag into one contiguous array as well
+  double* done = b->partials + (size_t)b->n * 64;
+  for (int par = 0; par < 2; ++par)
+    for (BatchStep& st : b->iter_steps[par])
+      if (st.kind == 2 && st.mode == KB_SCALARS)
+        for (int p = 0; p < st.ntasks; ++p) {
+          KTask* t = reinterpret_cast<KTask*>(b->host_tab.data() + st.off) + p;
+          t->c = done + p;
+        }
+  if (b->host_tab.size() > b->tab_bytes / 3 * 2) return b->fail(AGCA_EINTERNAL, "batch task table overflow");
+  BCK(cudaMemcpyAsync(b->tab, b->host_tab.data(), b->host_tab.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (b->iter_graph) {
+    cudaGraphExecDestroy(b->iter_graph);
+    b->iter_graph = nullptr;
+  }
+  b->iter_launches = 0;
+  if (b->stream != nullptr) {
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int64_t nl = 0;
+    agca_status st = run_steps(b, b->iter_steps[0], &nl);
+    if (st == AGCA_OK) st = run_steps(b, b->iter_steps[1], &nl);
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (st != AGCA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    BCK(ee);
+    const cudaError_t ie = cudaGraphInstantiate(&b->iter_graph, g, 0);
+    cudaGraphDestroy(g);
+    BCK(ie);
+    b->iter_launches = nl;
+  }
+  b->setup_done = true;
+  return AGCA_OK;
+}
+
+agca_status agca_batch_load_vector(agca_batch* b, int i, const double* fbar_dev, double* b_dev) {
+  if (!batch_valid(b, i)) return AGCA_EINVAL;
+  const agca_status st = agca_load_vector(b->ctx[i], fbar_dev, b_dev);
+  return st == AGCA_OK ? st : b->fail(st, b->ctx[i]->err);
+}
+
+agca_status agca_batch_vcycle(agca_batch* b, const double* const* r_devs, double* const* z_devs) {
+  if (!b || !r_devs || !z_devs) return AGCA_EINVAL;
+  if (!b->setup_done) return b->fail(AGCA_ESTATE, "setup first");
+  std::vector<const double*> r(r_devs, r_devs + b->n);
+  std::vector<double*> z(z_devs, z_devs + b->n);
+  std::vector<BatchStep> steps;
+  const size_t base = b->host_tab.size();
+  if (b->prec == AGCA_MIXED)
+    build_cycle<float>(b, steps, r, z, false);
+  else
+    build_cycle<double>(b, steps, r, z, false);
+  const size_t used = b->host_tab.size() - base;
+  if (b->host_tab.size() > b->tab_bytes) {
+    b->host_tab.resize(base);
+    return b->fail(AGCA_EINTERNAL, "batch task table overflow");
+  }
+  BCK(cudaMemcpyAsync(b->tab + base, b->host_tab.data() + base, used, cudaMemcpyHostToDevice, b->stream));
+  int64_t nl = 0;
+  const agca_status st = run_steps(b, steps, &nl);
+  BCK(cudaStreamSynchronize(b->stream));  // the table region is reused by the next call
+  b->host_tab.resize(base);
+  return st;
+}
+
+agca_status agca_batch_solve(agca_batch* b, const double* const* b_devs, double* const* x_devs, double rtol, int maxit,
+                             int* iters, double* relres) {
+  if (!b || !b_devs || !x_devs) return AGCA_EINVAL;
+  if (!b->setup_done) return b->fail(AGCA_ESTATE, "setup first");
+  if (!(rtol > 0.0) || maxit < 1) return b->fail(AGCA_EINVAL, "rtol must be > 0 and maxit >= 1");
+  const int P = b->n;
+  const bool mixed = b->prec == AGCA_MIXED;
+  std::vector<double> nb(P, 0.0), rel(P, 0.0);
+  std::vector<int> total(P, 0);
+  std::vector<char> active(P, 0);
+  static const double one = 1.0;
+  for (int p = 0; p < P; ++p) {
+    agca_ctx* ctx = b->ctx[p];
+    const int64_t nt = ctx->nt;
+    double* bm = ctx->kv[KV_B];
+    LK(1, launch_vec_op(VOP_COPY, nt, bm, b_devs[p], nullptr, nullptr, nullptr, b->stream));
+    LK(1, launch_mask_boundary(ctx->lev[ctx->L].n, bm, b->stream));
+    LK(1, launch_vec_op(VOP_ZERO, nt, x_devs[p], nullptr, nullptr, nullptr, nullptr, b->stream));
+    double nb2 = 0.0;
+    CKS(dot1(ctx, bm, bm, nt, ctx->sc + MS_TMP0));
+    CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nb2));
+    nb[p] = sqrt(nb2);
+    rel[p] = nb[p] > 0.0 ? 1.0 : 0.0;
+  }
+  double* done_dev = b->partials + (size_t)P * 64;
+  std::vector<double> done(P, 0.0);
+  for (int outer = 0; outer < 60; ++outer) {
+    bool any = false;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* ctx = b->ctx[p];
+      const int64_t nt = ctx->nt;
+      active[p] = 0;
+      if (!(nb[p] > 0.0)) continue;
+      CKS(stokes_dispatch(ctx, x_devs[p], ctx->kv[KV_KZ], false));
+      LK(1, launch_vec_op(VOP_SUB, nt, ctx->kv[KV_R], ctx->kv[KV_B], ctx->kv[KV_KZ], nullptr, nullptr, b->stream));
+      double nr2 = 0.0;
+      CKS(dot1(ctx, ctx->kv[KV_R], ctx->kv[KV_R], nt, ctx->sc + MS_TMP0));
+      CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nr2));
+      rel[p] = sqrt(nr2) / nb[p];
+      active[p] = (rel[p] > rtol && total[p] < maxit) ? 1 : 0;
+      any = any || active[p];
+    }
+    if (!any) break;
+    int budget = 0;
+    for (int p = 0; p < P; ++p) {
+      agca_ctx* ctx = b->ctx[p];
+      const int64_t nt = ctx->nt;
+      cudaStream_t s = b->stream;
+      if (!active[p]) {
+        CK(cudaMemcpyAsync(ctx->sc + MS_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->sc + MS_UPD_SKIP, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+        continue;
+      }
+      budget = std::max(budget, maxit - total[p]);
+      double inner = 0.1 * rtol / rel[p];
+      if (mixed) inner = std::max(inner, 1e-5);
+      inner = std::max(inner, 1e-14);
+      LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_D], nullptr, nullptr, nullptr, nullptr, s));
+      LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_VOLD], nullptr, nullptr, nullptr, nullptr, s));
+      LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_WOLD], nullptr, nullptr, nullptr, nullptr, s));
+      LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_W], nullptr, nullptr, nullptr, nullptr, s));
+      LK(1, launch_vec_op(VOP_COPY, nt, ctx->kv[KV_V], ctx->kv[KV_R], nullptr, nullptr, nullptr, s));
+      CKS(precond_impl(ctx, ctx->kv[KV_V], ctx->kv[KV_Z]));
+      CKS(dot1(ctx, ctx->kv[KV_Z], ctx->kv[KV_V], nt, ctx->sc + MS_DOT_ZV));
+      LK(1, launch_minres_init(ctx->sc, inner, s));
+    }
+    // lockstep iterations, two per graph replay (buffer parity returns)
+    int64_t launches = 0;
+    for (int it = 0; it < budget; it += 2) {
+      if (b->iter_graph) {
+        BCK(cudaGraphLaunch(b->iter_graph, b->stream));
+        launches += b->iter_launches;
+      } else {
+        BCKS(run_steps(b, b->iter_steps[0], &launches));
+        BCKS(run_steps(b, b->iter_steps[1], &launches));
+      }
+      if ((it / 2 + 1) % 4 == 0 || it + 2 >= budget) {
+        BCK(cudaMemcpyAsync(done.data(), done_dev, P * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        bool all = true;
+        for (int p = 0; p < P; ++p)
+          if (active[p] && done[p] == 0.0) all = false;
+        if (all) break;
+      }
+    }
+    for (int p = 0; p < P; ++p) {
+      if (!active[p]) continue;
+      agca_ctx* ctx = b->ctx[p];
+      double its = 0.0;
+      CKS(read_scalar(ctx, ctx->sc + MS_ITERS, &its));
+      total[p] += (int)its;
+      LK(1, launch_vec_op(VOP_ADD, ctx->nt, x_devs[p], x_devs[p], ctx->kv[KV_D], nullptr, nullptr, b->stream));
+      CKS(project_pressure(ctx, x_devs[p]));
+    }
+    b->ctx[0]->launches += launches;
+  }
+  bool ok = true;
+  for (int p = 0; p < P; ++p) {
+    if (iters) iters[p] = total[p];
+    if (relres) relres[p] = rel[p];
+    if (!(rel[p] <= rtol)) ok = false;
+  }
+  if (!ok) return b->fail(AGCA_ENOTCONV, "some problems stopped above the tolerance");
+  return AGCA_OK;
+}
+
+agca_ctx* agca_batch_context(agca_batch* b, int i) { return batch_valid(b, i) ? b->ctx[i] : nullptr; }
 
 }  // extern "C"

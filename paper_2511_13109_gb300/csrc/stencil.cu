@@ -20,6 +20,8 @@
 // each owner finishes its vertex in registers (owner-computes: no atomics,
 // deterministic summation order).  HBM traffic per vertex is one read of x,
 // the 6 element coefficients and the epilogue vectors, and one write.
+#include <algorithm>
+
 #include "agca_internal.cuh"
 
 namespace agca {
@@ -128,7 +130,7 @@ __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1
 
 template <int MODE, typename TS>
 __host__ __device__ constexpr int stencil_tile_fields() {
-  return MODE == ST_CHEB_PRE ? 6 : (MODE == ST_STOKES ? 4 : 3);
+  return MODE == ST_CHEB_PRE ? 9 : (MODE == ST_STOKES ? 4 : 3);
 }
 
 // dynamic shared memory of one block: tile ring [3][NF][(BX+1)(BY+1)] of TS,
@@ -145,14 +147,16 @@ __host__ __device__ constexpr size_t stencil_smem_bytes() {
          (size_t)2 * NC * BX * BY * sizeof(T);
 }
 
+// One CTA tile (bx, by, bz) of the stencil; called by the single-operator
+// kernel (tile = block index) and by the persistent batched kernel.
 template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
-__global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
-    stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch) {
+__device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const StencilArgs<TS>& a, const int zch,
+                                              const int bx, const int by, const int bz,
+                                              unsigned char* __restrict__ smem_raw) {
   constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;  // combined fields: velocity (+ divergence)
   constexpr int NF = stencil_tile_fields<MODE, TS>();
   constexpr int TW = BX + 1, TSZ = (BX + 1) * (BY + 1), NT = BX * BY;
   constexpr int NSLOT = (TSZ + NT - 1) / NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TS* xs = reinterpret_cast<TS*>(smem_raw);
   T* cfs = reinterpret_cast<T*>(smem_raw + stencil_tile_bytes<TS, BX, BY, MODE>());
   T* cs = cfs + 2 * NT * 6;
@@ -163,8 +167,8 @@ __global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
   const int64_t plane = (int64_t)nv * nv;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
-  const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
-  const int z0 = blockIdx.z * zch;
+  const int x0 = bx * (BX - 1), y0 = by * (BY - 1);
+  const int z0 = bz * zch;
   const int z1 = min(z0 + zch, nv);
   const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
   const bool cube_xy = (cx >= 0) && (cx < n) && (cy >= 0) && (cy < n);
@@ -229,8 +233,20 @@ __global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
       for (int i = 0; i < 3; ++i) cp_async(dst + 2 * i, src + 2 * i, 16, ok);
     }
   };
+  // CHEB_PRE: the first Chebyshev iterate x1 = s2 D^-1 b of the slots this
+  // thread copied, formed once in shared memory (fields 6..8)
+  auto convert_plane = [&](int z) {
+    TS* t = xs + ((z - zs) % 3) * NF * TSZ;
+#pragma unroll
+    for (int j = 0; j < NSLOT; ++j) {
+      if (!(s_flags & (1u << (2 * j)))) continue;
+      const int idx = tid + j * NT;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) t[(6 + c) * TSZ + idx] = a.s2 * t[(3 + c) * TSZ + idx] * t[c * TSZ + idx];
+    }
+  };
   auto tile_val = [&](const TS* t, int c, int li) -> T {
-    if (MODE == ST_CHEB_PRE) return (T)(a.s2 * t[(3 + c) * TSZ + li] * t[c * TSZ + li]);
+    if (MODE == ST_CHEB_PRE) return (T)t[(6 + c) * TSZ + li];
     return (T)t[c * TSZ + li];
   };
 
@@ -278,6 +294,10 @@ __global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
       }
     }
     cp_wait1();
+    if (MODE == ST_CHEB_PRE) {
+      if (k == zs) convert_plane(zs);
+      if (k + 1 <= n) convert_plane(k + 1);
+    }
     __syncthreads();
     {
       const TS* tl = xs + ((k - zs) % 3) * NF * TSZ;
@@ -388,14 +408,44 @@ __global__ void __launch_bounds__(BX* BY, sizeof(T) == 4 ? 3 : 2)
   }
 }
 
+template <typename T, int BY>
+__host__ __device__ constexpr int stencil_min_blocks() {
+  return sizeof(T) == 4 ? (BY <= 8 ? 3 : (BY <= 12 ? 2 : 1)) : 2;
+}
+
+template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
+__global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
+    stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stencil_block<TS, T, BX, BY, MODE, COARSE>(op, a, zch, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Persistent batched form: one launch applies the same stencil mode to many
+// independent problems; every CTA walks the flattened (problem, tile) work
+// list, skipping problems whose MINRES has converged.
+template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
+__global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
+    stencil_batch_kernel(const StencilTask<TS, T>* __restrict__ tasks, const int ntasks, const int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    int j = 0;
+    while (j + 1 < ntasks && tasks[j + 1].tile0 <= it) ++j;
+    const StencilTask<TS, T> tk = tasks[j];
+    if (tk.sc && tk.sc[MS_DONE] != 0.0) continue;  // converged problem
+    const int64_t local = it - tk.tile0;
+    const int bx = (int)(local % tk.gx), by = (int)((local / tk.gx) % tk.gy), bz = (int)(local / ((int64_t)tk.gx * tk.gy));
+    stencil_block<TS, T, BX, BY, MODE, COARSE>(tk.op, tk.a, tk.zch, bx, by, bz, smem_raw);
+    __syncthreads();  // the shared-memory rings are reused by the next tile
+  }
+}
+
+
 // Flagged elements of a coarse level: y_e = s_e A_e x_e (Eq. 2.9, stored
 // Galerkin part), one thread per (element, row), written to op.ye for the
 // stencil kernel to scatter.  x follows the stencil's input convention
 // (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).
 template <typename TS, typename T, bool PRE>
-__global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= op.n_flag * 12) return;
+__device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
   const int64_t f = id / 12;
   const int r = (int)(id % 12);
   const int64_t e = op.list[f];
@@ -427,17 +477,26 @@ __global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
   op.ye[f * 12 + r] = op.gscale ? op.gscale[f] * acc : acc;
 }
 
+template <typename TS, typename T, bool PRE>
+__global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= op.n_flag * 12) return;
+  gca_row<TS, T, PRE>(op, a, id);
+}
+
+template <typename TS, typename T, bool PRE>
+__global__ void gca_apply_batch_kernel(const StencilTask<TS, T>* __restrict__ tasks) {
+  const StencilTask<TS, T>& tk = tasks[blockIdx.y];
+  if (tk.sc && tk.sc[MS_DONE] != 0.0) return;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= tk.op.n_flag * 12) return;
+  gca_row<TS, T, PRE>(tk.op, tk.a, id);
+}
+
 template <typename TS, typename T, int BX, int BY, bool COARSE>
-cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s) {
-  const int nv = op.n + 1;
-  const int gx = (nv + BX - 2) / (BX - 1), gy = (nv + BY - 2) / (BY - 1);
-  // enough blocks for two waves of 3 resident blocks per SM; small grids get
-  // short z-chunks (latency bound), large ones long chunks (less z-halo)
-  int gz = (912 + gx * gy - 1) / (gx * gy);
-  int zch = (nv + gz - 1) / gz;
-  if (zch < 1) zch = 1;
-  if (zch > nv) zch = nv;
-  gz = (nv + zch - 1) / zch;
+cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s, int zch_req) {
+  int gx, gy, gz, zch;
+  stencil_grid_by(op.n, BY, zch_req, &gx, &gy, &gz, &zch);
   if (COARSE && op.n_flag > 0) {
     const int64_t nth = op.n_flag * 12;
     const unsigned gb = (unsigned)((nth + 127) / 128);
@@ -481,19 +540,116 @@ cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a
   return cudaGetLastError();
 }
 
+template <typename TS, typename T, int BX, int BY, bool COARSE>
+cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
+                              int64_t max_gca_rows, cudaStream_t s) {
+  if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
+  if (COARSE && max_gca_rows > 0) {
+    dim3 g((unsigned)((max_gca_rows + 127) / 128), (unsigned)ntasks);
+    if (mode == ST_CHEB_PRE)
+      gca_apply_batch_kernel<TS, T, true><<<g, 128, 0, s>>>(tasks);
+    else
+      gca_apply_batch_kernel<TS, T, false><<<g, 128, 0, s>>>(tasks);
+  }
+  int dev = 0, sms = 152;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int per_sm = sizeof(T) == 4 ? 3 : 2;
+  const int64_t nb = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  dim3 grid((unsigned)nb), block(BX, BY);
+#define AGCA_BLAUNCH(M, C)                                                                                 \
+  do {                                                                                                     \
+    constexpr size_t smem = stencil_smem_bytes<TS, T, BX, BY, M>();                                       \
+    static bool attr_set[64] = {};                                                                        \
+    if (smem > 48 * 1024 && dev >= 0 && dev < 64 && !attr_set[dev]) {                                    \
+      e = cudaFuncSetAttribute(stencil_batch_kernel<TS, T, BX, BY, M, C>,                                 \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
+      if (e != cudaSuccess) return e;                                                                     \
+      attr_set[dev] = true;                                                                               \
+    }                                                                                                     \
+    stencil_batch_kernel<TS, T, BX, BY, M, C><<<grid, block, smem, s>>>(tasks, ntasks, ntiles);  \
+  } while (0)
+  switch (mode) {
+    case ST_RESID: AGCA_BLAUNCH(ST_RESID, COARSE); break;
+    case ST_CHEB_FIRST: AGCA_BLAUNCH(ST_CHEB_FIRST, COARSE); break;
+    case ST_CHEB_STEP: AGCA_BLAUNCH(ST_CHEB_STEP, COARSE); break;
+    case ST_CHEB_PRE: AGCA_BLAUNCH(ST_CHEB_PRE, COARSE); break;
+    case ST_STOKES:
+      if constexpr (COARSE) {
+        return cudaErrorInvalidValue;
+      } else {
+        AGCA_BLAUNCH(ST_STOKES, false);
+      }
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AGCA_BLAUNCH
+  return cudaGetLastError();
+}
+
 }  // namespace
 
+void stencil_grid(int n, int* gx_out, int* gy_out, int* gz_out, int* zch_out) {
+  stencil_grid_by(n, 8, 0, gx_out, gy_out, gz_out, zch_out);
+}
+
+void stencil_grid_by(int n, int BY, int zch_req, int* gx_out, int* gy_out, int* gz_out, int* zch_out) {
+  constexpr int BX = 32;
+  const int nv = n + 1;
+  const int gx = (nv + BX - 2) / (BX - 1), gy = (nv + BY - 2) / (BY - 1);
+  // default: enough blocks for two waves of 3 resident 256-thread blocks per
+  // SM; small grids get short z-chunks (latency bound), large ones long
+  // chunks (less z-halo).  zch_req > 0 (autotuner) overrides.
+  int gz = (912 * 8 / BY + gx * gy - 1) / (gx * gy);
+  int zch = zch_req > 0 ? zch_req : (nv + gz - 1) / gz;
+  if (zch < 1) zch = 1;
+  if (zch > nv) zch = nv;
+  gz = (nv + zch - 1) / zch;
+  *gx_out = gx;
+  *gy_out = gy;
+  *gz_out = gz;
+  *zch_out = zch;
+}
+
 template <typename TS, typename T>
-cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s) {
-  if (op.fidx) return launch_mode<TS, T, 32, 8, true>(mode, op, a, s);
-  return launch_mode<TS, T, 32, 8, false>(mode, op, a, s);
+cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
+                                 int64_t max_gca_rows, cudaStream_t s) {
+  if (coarse) return launch_batch_mode<TS, T, 32, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
+  return launch_batch_mode<TS, T, 32, 8, false>(mode, tasks, ntasks, ntiles, 0, s);
+}
+template cudaError_t launch_stencil_batch<float, float>(int, bool, const StencilTask<float, float>*, int, int64_t,
+                                                        int64_t, cudaStream_t);
+template cudaError_t launch_stencil_batch<double, double>(int, bool, const StencilTask<double, double>*, int, int64_t,
+                                                          int64_t, cudaStream_t);
+template cudaError_t launch_stencil_batch<double, float>(int, bool, const StencilTask<double, float>*, int, int64_t,
+                                                         int64_t, cudaStream_t);
+
+template <typename TS, typename T>
+cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s,
+                           const TileCfg* cfg) {
+  const int by = cfg ? cfg->by : 8, zch = cfg ? cfg->zch : 0;
+  if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
+    if (by == 12) {
+      if (op.fidx) return launch_mode<TS, T, 32, 12, true>(mode, op, a, s, zch);
+      return launch_mode<TS, T, 32, 12, false>(mode, op, a, s, zch);
+    }
+    if (by == 16) {
+      if (op.fidx) return launch_mode<TS, T, 32, 16, true>(mode, op, a, s, zch);
+      return launch_mode<TS, T, 32, 16, false>(mode, op, a, s, zch);
+    }
+  }
+  if (by != 8) return cudaErrorInvalidValue;
+  if (op.fidx) return launch_mode<TS, T, 32, 8, true>(mode, op, a, s, zch);
+  return launch_mode<TS, T, 32, 8, false>(mode, op, a, s, zch);
 }
 
 template cudaError_t launch_stencil<float, float>(int, const LevelOp<float>&, const StencilArgs<float>&,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const TileCfg*);
 template cudaError_t launch_stencil<double, double>(int, const LevelOp<double>&, const StencilArgs<double>&,
-                                                    cudaStream_t);
+                                                    cudaStream_t, const TileCfg*);
 template cudaError_t launch_stencil<double, float>(int, const LevelOp<float>&, const StencilArgs<double>&,
-                                                   cudaStream_t);
+                                                   cudaStream_t, const TileCfg*);
 
 }  // namespace agca
