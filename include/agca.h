@@ -102,6 +102,13 @@ const char* agca_last_error(const agca_ctx* ctx);
  * for lambda_hat.  Defaults 2, 0.1, 1.1, 20.  Call before agca_setup. */
 agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, int power_iters);
 
+/* Solver options: in mixed contexts each residual-refinement step runs
+ * MINRES until the preconditioned residual norm has dropped by at least
+ * mixed_inner_rtol (default 1e-5; the FP32 cycle and operator limit how far
+ * one inner solve can usefully go); check_every MINRES iterations pass
+ * between host-side convergence checks (default 4). */
+agca_status agca_set_solver_options(agca_ctx* ctx, double mixed_inner_rtol, int check_every);
+
 /* Bytes of device workspace the context needs (excluding the Galerkin store). */
 agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes);
 /* Bind caller-owned device memory of at least agca_workspace_size bytes,

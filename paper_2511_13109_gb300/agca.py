@@ -46,6 +46,7 @@ _SIGS = {
     "agca_destroy": ([_P], None),
     "agca_last_error": ([_P], ctypes.c_char_p),
     "agca_set_smoother": ([_P, _I, _D, _D, _I], _I),
+    "agca_set_solver_options": ([_P, _D, _I], _I),
     "agca_workspace_size": ([_P, ctypes.POINTER(_SZ)], _I),
     "agca_bind_workspace": ([_P, _P, _SZ], _I),
     "agca_set_viscosity": ([_P, _P], _I),
@@ -205,6 +206,10 @@ class Context:
     # ---- setup ---------------------------------------------------------------
     def set_smoother(self, degree=2, lo=0.1, hi=1.1, power_iters=20):
         self._check(lib().agca_set_smoother(self._h, degree, lo, hi, power_iters), "set_smoother")
+
+    def set_solver_options(self, mixed_inner_rtol: float = 1e-5, check_every: int = 4):
+        self._check(lib().agca_set_solver_options(self._h, float(mixed_inner_rtol), int(check_every)),
+                    "set_solver_options")
 
     def set_viscosity(self, eta: torch.Tensor):
         _need(eta, self.E[self.L], torch.float64, "eta")

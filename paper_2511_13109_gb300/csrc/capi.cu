@@ -62,6 +62,8 @@ struct agca_ctx {
   int cheb_degree = 2;
   double cheb_lo = 0.1, cheb_hi = 1.1;
   int power_iters = 20;
+  double mixed_inner = 1e-5;  // floor of the inner MINRES tolerance in mixed refinement
+  int check_every = 4;        // MINRES iterations between host convergence checks
   std::vector<Level> lev;  // 1..L
   // workspace
   char* ws = nullptr;
@@ -520,7 +522,7 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
   CKS(precond_impl(ctx, v, z));
   CKS(dot1(ctx, z, v, nt, ctx->sc + MS_DOT_ZV));
   LK(1, launch_minres_init(ctx->sc, tol_rel, s));
-  const int check_every = 4;
+  const int check_every = ctx->check_every;
   int it = 0;
   for (; it < maxit; ++it) {
     CKS(stokes_dispatch(ctx, z, kz, low));
@@ -581,7 +583,7 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
     rel = sqrt(nr2) / nb;
     if (!(rel > rtol) || total >= maxit) break;
     double inner = 0.1 * rtol / rel;
-    if (mixed) inner = std::max(inner, 1e-5);
+    if (mixed) inner = std::max(inner, ctx->mixed_inner);
     inner = std::max(inner, 1e-14);
     int its = 0;
     CKS(minres_impl(ctx, r, d, inner, maxit - total, mixed, &its));
@@ -1156,6 +1158,15 @@ agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, i
   ctx->cheb_hi = hi;
   ctx->power_iters = power_iters;
   ctx->setup_done = false;
+  return AGCA_OK;
+}
+
+agca_status agca_set_solver_options(agca_ctx* ctx, double mixed_inner_rtol, int check_every) {
+  if (!ctx) return AGCA_EINVAL;
+  if (!(mixed_inner_rtol > 0.0 && mixed_inner_rtol < 1.0) || check_every < 1 || check_every > 1000)
+    return ctx->fail(AGCA_EINVAL, "solver options out of range");
+  ctx->mixed_inner = mixed_inner_rtol;
+  ctx->check_every = check_every;
   return AGCA_OK;
 }
 
@@ -1741,7 +1752,7 @@ agca_status agca_batch_solve(agca_batch* b, const double* const* b_devs, double*
       }
       budget = std::max(budget, maxit - total[p]);
       double inner = 0.1 * rtol / rel[p];
-      if (mixed) inner = std::max(inner, 1e-5);
+      if (mixed) inner = std::max(inner, ctx->mixed_inner);
       inner = std::max(inner, 1e-14);
       LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_D], nullptr, nullptr, nullptr, nullptr, s));
       LK(1, launch_vec_op(VOP_ZERO, nt, ctx->kv[KV_VOLD], nullptr, nullptr, nullptr, nullptr, s));

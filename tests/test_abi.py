@@ -55,6 +55,9 @@ def test_host_only_calls(libagca):
     assert L.agca_setup(h) == 7
     assert L.agca_set_smoother(h, 1, 0.3, 1.2, 20) == 1
     assert b"smoother" in L.agca_last_error(h)
+    assert L.agca_set_solver_options(h, 0.0, 4) == 1
+    assert L.agca_set_solver_options(h, 1e-4, 0) == 1
+    assert L.agca_set_solver_options(h, 1e-4, 8) == 0
     L.agca_destroy(h)
     bad = ctypes.c_void_p()
     assert L.agca_create(16, 6, 0, None, ctypes.byref(bad)) == 1   # 32 cubes cannot coarsen 5 times to >= 2
