@@ -104,7 +104,7 @@ agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, i
 
 /* Solver options: in mixed contexts each residual-refinement step runs
  * MINRES until the preconditioned residual norm has dropped by at least
- * mixed_inner_rtol (default 1e-5; the FP32 cycle and operator limit how far
+ * mixed_inner_rtol (default 1e-4; the FP32 cycle and operator limit how far
  * one inner solve can usefully go); check_every MINRES iterations pass
  * between host-side convergence checks (default 4). */
 agca_status agca_set_solver_options(agca_ctx* ctx, double mixed_inner_rtol, int check_every);
@@ -210,6 +210,12 @@ agca_status agca_stokes_apply_static(int N, const double* eta_dev, const double*
 agca_status agca_autotune(agca_ctx* ctx, int reps, const char* cache_path);
 /* The tile shape in use for (level, mode): block rows and z-chunk (0 = automatic). */
 agca_status agca_tile_config(const agca_ctx* ctx, int level, int mode, int* by, int* zch);
+/* Set the tile shape of (level, mode) by hand (mode 5: the Stokes operator
+ * on the finest level): by = 8, 12 or 16 block rows (12 and 16 in FP32 only),
+ * zch = z-chunk in vertex planes (0 = automatic, at most 4096).  Results do
+ * not depend on the tile shape: every vertex sums its element contributions
+ * in the same order.  Host only; AGCA_EINVAL for other values. */
+agca_status agca_set_tile_config(agca_ctx* ctx, int level, int mode, int by, int zch);
 
 /* Number of CUDA kernels this context has launched so far (host counter). */
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);

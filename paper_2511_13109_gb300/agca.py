@@ -66,6 +66,7 @@ _SIGS = {
     "agca_stokes_apply_static": ([_I, _P, _P, _P, _P], _I),
     "agca_autotune": ([_P, _I, ctypes.c_char_p], _I),
     "agca_tile_config": ([_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "agca_set_tile_config": ([_P, _I, _I, _I, _I], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
@@ -207,7 +208,7 @@ class Context:
     def set_smoother(self, degree=2, lo=0.1, hi=1.1, power_iters=20):
         self._check(lib().agca_set_smoother(self._h, degree, lo, hi, power_iters), "set_smoother")
 
-    def set_solver_options(self, mixed_inner_rtol: float = 1e-5, check_every: int = 4):
+    def set_solver_options(self, mixed_inner_rtol: float = 1e-4, check_every: int = 4):
         self._check(lib().agca_set_solver_options(self._h, float(mixed_inner_rtol), int(check_every)),
                     "set_solver_options")
 
@@ -309,6 +310,11 @@ class Context:
         return g, its.value
 
     # ---- introspection ---------------------------------------------------------
+    def set_tile_config(self, level: int, mode: int, block_rows: int = 8, z_chunk: int = 0):
+        """Fix the tile shape of one (level, stencil mode) launch by hand."""
+        self._check(lib().agca_set_tile_config(self._h, int(level), int(mode), int(block_rows), int(z_chunk)),
+                    "set_tile_config")
+
     def autotune(self, reps: int = 10, cache: str | None = None) -> dict:
         """Pick the tile shape of every V-cycle stencil launch by timing
         (agca_autotune); returns {(level, mode): (block_rows, z_chunk)}."""

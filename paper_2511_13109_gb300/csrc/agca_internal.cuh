@@ -84,6 +84,46 @@ struct LevelOp {
 __host__ __device__ inline int64_t nverts(int n) { return (int64_t)(n + 1) * (n + 1) * (n + 1); }
 __host__ __device__ inline int64_t nelems(int n) { return (int64_t)6 * n * n * n; }
 
+// ---------------------------------------------------------------- dependent launch
+// Programmatic dependent launch: a hot-path kernel is launched while its
+// predecessor in the stream is still running, so the launch latency of the
+// ~50 short kernels of a V-cycle or MINRES iteration overlaps the previous
+// kernel.  Every kernel begins with grid_dep_entry(): each thread waits until
+// all grids it depends on have completed and their writes are visible (a
+// no-op when the kernel was launched normally), then allows the next grid to
+// begin launching.  Waiting in every thread before any memory access keeps
+// the stream's ordering transitive (a grid completes only after the grids
+// before it) and rules out write-after-read races with the predecessor.
+__device__ __forceinline__ void grid_dep_entry() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// Whether launches carry the programmatic-serialization attribute (on unless
+// the environment sets AGCA_PDL=0; never on the legacy default stream).
+bool pdl_enabled(cudaStream_t s);
+
+template <typename... KP, typename... A>
+cudaError_t launch_k(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled(s) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+// return the error of a launch from the enclosing cudaError_t function
+#define KL(...)                                  \
+  do {                                           \
+    const cudaError_t e_ = (__VA_ARGS__);        \
+    if (e_ != cudaSuccess) return e_;            \
+  } while (0)
+
 // ---------------------------------------------------------------- launchers
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_CHEB_FIRST = 2, ST_CHEB_STEP = 3, ST_CHEB_PRE = 4, ST_STOKES = 5 };
 
@@ -96,6 +136,7 @@ struct StencilArgs {
   const T* q;      // fine-grid pressure P p (STOKES)
   T* out;
   T* out2;         // B_f u on the fine grid (STOKES)
+  double* out64;   // if set, the result is written here widened to FP64 instead of to out
   T s0, s1, s2;    // mode scalars
 };
 
@@ -124,8 +165,17 @@ struct StencilTask {
 // tile decomposition used by both the single and the batched launch
 void stencil_grid(int n, int* gx, int* gy, int* gz, int* zch);
 void stencil_grid_by(int n, int by, int zch_req, int* gx, int* gy, int* gz, int* zch);
-// tasks: device array, ntiles = total tiles; launches the gca_apply part too
-// when coarse (gtasks: the same tasks, one per problem with flagged elements)
+// Tiles of a single-operator launch: wide tiles (32 x BY threads) over vertex
+// columns 0 .. 31*gxw-1, narrow tiles (8 x 4BY threads) over x0n .. n; grid =
+// (per_z(), gz) blocks of 32*BY threads.
+struct TileGrid {
+  int gxw = 0, gyw = 0, gxn = 0, gyn = 0, x0n = 0, gz = 0, zch = 0;
+  int per_z() const { return gxw * gyw + gxn * gyn; }
+};
+TileGrid stencil_tiles(int n, int by, int zch_req);
+// tasks: device array, ntiles = total tiles of all tasks; coarse launches
+// first run the stored-Galerkin products of every task (max_gca_rows = the
+// largest n_flag * 12)
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s);

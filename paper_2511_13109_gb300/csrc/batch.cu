@@ -20,6 +20,7 @@ __device__ __forceinline__ bool skip(const double* sc) { return sc && sc[MS_DONE
 
 template <typename T>
 __global__ void restrict_batch_kernel(const XferTask* __restrict__ tasks) {
+  grid_dep_entry();
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
   const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
@@ -52,6 +53,7 @@ __global__ void restrict_batch_kernel(const XferTask* __restrict__ tasks) {
 
 template <typename T, bool ADD>
 __global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
+  grid_dep_entry();
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
   const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
@@ -79,6 +81,7 @@ __global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
 
 template <typename TI, typename TO>
 __global__ void convert_batch_kernel(const XferTask* __restrict__ tasks) {
+  grid_dep_entry();
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
   const TI* in = static_cast<const TI*>(tk.src);
@@ -90,6 +93,7 @@ __global__ void convert_batch_kernel(const XferTask* __restrict__ tasks) {
 // coarsest solves, one block per problem (as coarse_solve_kernel)
 template <typename T>
 __global__ void coarse_solve_batch_kernel(const XferTask* __restrict__ tasks) {
+  grid_dep_entry();
   extern __shared__ double sm[];
   const XferTask tk = tasks[blockIdx.x];
   if (skip(tk.sc)) return;
@@ -139,6 +143,7 @@ __global__ void coarse_solve_batch_kernel(const XferTask* __restrict__ tasks) {
 // ------------------------------------------------------------------ Krylov
 template <int OP>
 __global__ void __launch_bounds__(kBT) reduce_batch_kernel(const KTask* __restrict__ tasks, double* partials) {
+  grid_dep_entry();
   const KTask tk = tasks[blockIdx.y];
   double acc = 0.0;
   if (!skip(tk.sc)) {
@@ -159,6 +164,7 @@ __global__ void __launch_bounds__(kBT) reduce_batch_kernel(const KTask* __restri
 }
 
 __global__ void reduce_batch_final_kernel(const KTask* __restrict__ tasks, const double* partials) {
+  grid_dep_entry();
   const KTask tk = tasks[blockIdx.x];
   if (skip(tk.sc)) return;
   __shared__ double red[kDotBlocks];
@@ -172,6 +178,7 @@ __global__ void reduce_batch_final_kernel(const KTask* __restrict__ tasks, const
 }
 
 __global__ void vec_batch_kernel(const KTask* __restrict__ tasks, int op) {
+  grid_dep_entry();
   const KTask tk = tasks[blockIdx.y];
   if (op == KB_UPDATE ? tk.sc[MS_UPD_SKIP] != 0.0 : skip(tk.sc)) return;
   const double* sc = tk.sc;
@@ -239,6 +246,7 @@ __device__ void scalars_one(double* sc) {
 }
 
 __global__ void scalars_batch_kernel(const KTask* __restrict__ tasks, int ntasks) {
+  grid_dep_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ntasks) return;
   double* sc = tasks[p].sc;
@@ -255,16 +263,23 @@ template <typename T>
 cudaError_t launch_xfer_batch(int kind, const XferTask* tasks, int ntasks, int64_t max_count, int max_m,
                               cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
-  dim3 g(chunks(max_count, kBT), (unsigned)ntasks);
+  const dim3 g(chunks(max_count, kBT), (unsigned)ntasks);
+  const dim3 gc(std::min<unsigned>(g.x, 1216u), (unsigned)ntasks);
   switch (kind) {
-    case XK_RESTRICT: restrict_batch_kernel<T><<<g, kBT, 0, s>>>(tasks); break;
-    case XK_PROLONG_ADD: prolong_batch_kernel<T, true><<<g, kBT, 0, s>>>(tasks); break;
-    case XK_PROLONG: prolong_batch_kernel<T, false><<<g, kBT, 0, s>>>(tasks); break;
-    case XK_COPY64: convert_batch_kernel<double, double><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
-    case XK_D2F: convert_batch_kernel<double, float><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
-    case XK_F2D: convert_batch_kernel<float, double><<<dim3(std::min<unsigned>(g.x, 1216u), ntasks), kBT, 0, s>>>(tasks); break;
+    case XK_RESTRICT: KL(launch_k(restrict_batch_kernel<T>, g, dim3(kBT), 0, s, tasks)); break;
+    case XK_PROLONG_ADD: KL(launch_k(prolong_batch_kernel<T, true>, g, dim3(kBT), 0, s, tasks)); break;
+    case XK_PROLONG: KL(launch_k(prolong_batch_kernel<T, false>, g, dim3(kBT), 0, s, tasks)); break;
+    case XK_COPY64:
+      KL(launch_k(convert_batch_kernel<double, double>, gc, dim3(kBT), 0, s, tasks));
+      break;
+    case XK_D2F:
+      KL(launch_k(convert_batch_kernel<double, float>, gc, dim3(kBT), 0, s, tasks));
+      break;
+    case XK_F2D:
+      KL(launch_k(convert_batch_kernel<float, double>, gc, dim3(kBT), 0, s, tasks));
+      break;
     case XK_COARSE:
-      coarse_solve_batch_kernel<T><<<ntasks, 1024, 2 * (size_t)max_m * sizeof(double), s>>>(tasks);
+      KL(launch_k(coarse_solve_batch_kernel<T>, dim3(ntasks), dim3(1024), 2 * (size_t)max_m * sizeof(double), s, tasks));
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -278,17 +293,18 @@ cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t 
   if (ntasks <= 0) return cudaSuccess;
   switch (op) {
     case KB_DOT:
-      reduce_batch_kernel<KB_DOT><<<dim3(kDotBlocks, ntasks), kBT, 0, s>>>(tasks, partials);
-      reduce_batch_final_kernel<<<ntasks, kDotBlocks, 0, s>>>(tasks, partials);
+      KL(launch_k(reduce_batch_kernel<KB_DOT>, dim3(kDotBlocks, ntasks), dim3(kBT), 0, s, tasks, partials));
+      KL(launch_k(reduce_batch_final_kernel, dim3(ntasks), dim3(kDotBlocks), 0, s, tasks, partials));
       break;
     case KB_SUM:
-      reduce_batch_kernel<KB_SUM><<<dim3(kDotBlocks, ntasks), kBT, 0, s>>>(tasks, partials);
-      reduce_batch_final_kernel<<<ntasks, kDotBlocks, 0, s>>>(tasks, partials);
+      KL(launch_k(reduce_batch_kernel<KB_SUM>, dim3(kDotBlocks, ntasks), dim3(kBT), 0, s, tasks, partials));
+      KL(launch_k(reduce_batch_final_kernel, dim3(ntasks), dim3(kDotBlocks), 0, s, tasks, partials));
       break;
-    case KB_SCALARS: scalars_batch_kernel<<<chunks(ntasks, 32), 32, 0, s>>>(tasks, ntasks); break;
+    case KB_SCALARS: KL(launch_k(scalars_batch_kernel, dim3(chunks(ntasks, 32)), dim3(32), 0, s,
+                        tasks, ntasks)); break;
     default: {
       dim3 g(std::min<unsigned>(chunks(max_n, kBT), 1216u), (unsigned)ntasks);
-      vec_batch_kernel<<<g, kBT, 0, s>>>(tasks, op);
+      KL(launch_k(vec_batch_kernel, dim3(g), dim3(kBT), 0, s, tasks, op));
     }
   }
   return cudaGetLastError();

@@ -62,7 +62,7 @@ struct agca_ctx {
   int cheb_degree = 2;
   double cheb_lo = 0.1, cheb_hi = 1.1;
   int power_iters = 20;
-  double mixed_inner = 1e-5;  // floor of the inner MINRES tolerance in mixed refinement
+  double mixed_inner = 1e-4;  // floor of the inner MINRES tolerance in mixed refinement
   int check_every = 4;        // MINRES iterations between host convergence checks
   std::vector<Level> lev;  // 1..L
   // workspace
@@ -305,7 +305,7 @@ double stencil_bytes(int mode, size_t s) {
 
 template <typename T>
 agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, const T* xprev, T* out, double s0,
-                    double s1, double s2) {
+                    double s1, double s2, double* out64 = nullptr) {
   const Level& lv = ctx->lev[l];
   StencilArgs<T> a{};
   a.x = x;
@@ -313,6 +313,7 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
   a.invD = invD_of<T>(lv);
   a.xprev = xprev;
   a.out = out;
+  a.out64 = out64;
   a.s0 = (T)s0;
   a.s1 = (T)s1;
   a.s2 = (T)s2;
@@ -323,7 +324,9 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
   if (timed) {
     CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
     ctx->ev_used += 2;
-    ctx->prof_bytes += stencil_bytes(mode, sizeof(T)) * (double)lv.V;
+    // an FP64-widened result writes 3 * (8 - sizeof(T)) more bytes per vertex
+    const double wide = out64 ? 3.0 * (sizeof(double) - sizeof(T)) : 0.0;
+    ctx->prof_bytes += (stencil_bytes(mode, sizeof(T)) + wide) * (double)lv.V;
     ctx->prof_launches += 1;
   }
   return AGCA_OK;
@@ -332,8 +335,11 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
 // Chebyshev smoothing of A_l x = b (Section 4).  from_zero: start at x = 0
 // (the result of the first step is staged on the fly); otherwise start at
 // *cur.  cur/other are the two iterate buffers; returns the result buffer.
+// final64: if set, the last step writes its result there, widened to FP64,
+// instead of to the iterate buffers (the end of a mixed-precision cycle).
 template <typename T>
-agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur, T** other) {
+agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur, T** other,
+                      double* final64 = nullptr) {
   const Cheb c = cheb_params(ctx, l);
   const int k = ctx->cheb_degree;
   double rho = 1.0 / c.sigma;
@@ -345,12 +351,14 @@ agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur,
   }
   if (from_zero) CK(cudaMemsetAsync(*cur, 0, 3 * ctx->lev[l].V * sizeof(T), ctx->stream));
   // first step: other = cur + D^-1 (b - A cur) / theta
-  CKS(stencil<T>(ctx, ST_CHEB_FIRST, l, *cur, b, nullptr, *other, 1.0 / c.theta, 0.0, 0.0));
+  CKS(stencil<T>(ctx, ST_CHEB_FIRST, l, *cur, b, nullptr, *other, 1.0 / c.theta, 0.0, 0.0,
+                 k == 1 ? final64 : nullptr));
   std::swap(*cur, *other);  // cur = x1, other = x0
   for (step = 1; step < k; ++step) {
     const double rn = 1.0 / (2.0 * c.sigma - rho);
     // x_{i+1} = x_i + rn*rho (x_i - x_{i-1}) + (2 rn / delta) D^-1 (b - A x_i), written over x_{i-1}
-    CKS(stencil<T>(ctx, ST_CHEB_STEP, l, *cur, b, *other, *other, rn * rho, 2.0 * rn / c.delta, 0.0));
+    CKS(stencil<T>(ctx, ST_CHEB_STEP, l, *cur, b, *other, *other, rn * rho, 2.0 * rn / c.delta, 0.0,
+                   step + 1 == k ? final64 : nullptr));
     std::swap(*cur, *other);
     rho = rn;
   }
@@ -358,9 +366,9 @@ agca_status chebyshev(agca_ctx* ctx, int l, const T* b, bool from_zero, T** cur,
 }
 
 // V-cycle on level l for rhs b; X, Tb are the iterate buffers.  Returns the
-// buffer holding the result in *res.
+// buffer holding the result in *res, or writes it to final64 (FP64) if set.
 template <typename T>
-agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
+agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res, double* final64 = nullptr) {
   if (l == 1) {
     LK(1, launch_coarse_solve<T>(ctx->lev[1].n, ctx->linv_cm, ctx->linv_rm, b, X, ctx->stream));
     *res = X;
@@ -378,7 +386,7 @@ agca_status cycle(agca_ctx* ctx, int l, const T* b, T* X, T* Tb, T** res) {
   T* ec = nullptr;
   CKS(cycle<T>(ctx, l - 1, bc, static_cast<T*>(lc.vx), static_cast<T*>(lc.vt), &ec));
   LK(1, launch_prolong<T>(lv.n, 3, true, true, ec, cur, ctx->stream));
-  CKS(chebyshev<T>(ctx, l, b, false, &cur, &other));
+  CKS(chebyshev<T>(ctx, l, b, false, &cur, &other, final64));
   *res = cur;
   return AGCA_OK;
 }
@@ -395,8 +403,7 @@ agca_status vcycle_direct(agca_ctx* ctx, const double* r, double* z) {
     float* b32 = static_cast<float*>(lf.vb);
     LK(1, launch_d2f(r, b32, n3, ctx->stream));
     float* res = nullptr;
-    CKS(cycle<float>(ctx, L, b32, static_cast<float*>(lf.vx), static_cast<float*>(lf.vt), &res));
-    LK(1, launch_f2d(res, z, n3, ctx->stream));
+    CKS(cycle<float>(ctx, L, b32, static_cast<float*>(lf.vx), static_cast<float*>(lf.vt), &res, z));
   }
   return AGCA_OK;
 }
@@ -666,8 +673,7 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
       int last_zch = -1;
       for (int zr : zs) {
         if (zr > nv) continue;
-        int gx, gy, gz, zch;
-        stencil_grid_by(lv.n, by, zr, &gx, &gy, &gz, &zch);
+        const int zch = stencil_tiles(lv.n, by, zr).zch;
         if (zch == last_zch) continue;
         last_zch = zch;
         TileCfg c;
@@ -1424,6 +1430,18 @@ agca_status agca_tile_config(const agca_ctx* ctx, int level, int mode, int* by, 
   if (!ctx || !by || !zch || level < 1 || level > ctx->L || mode < 0 || mode > 5) return AGCA_EINVAL;
   *by = ctx->tune[level][mode].by;
   *zch = ctx->tune[level][mode].zch;
+  return AGCA_OK;
+}
+
+agca_status agca_set_tile_config(agca_ctx* ctx, int level, int mode, int by, int zch) {
+  if (!ctx) return AGCA_EINVAL;
+  if (level < 1 || level > ctx->L || mode < 0 || mode > 5 || zch < 0 || zch > 4096)
+    return ctx->fail(AGCA_EINVAL, "tile config out of range");
+  if (!(by == 8 || ((by == 12 || by == 16) && ctx->prec == AGCA_MIXED && mode != ST_STOKES)))
+    return ctx->fail(AGCA_EINVAL, "block rows must be 8 (or 12, 16 for FP32 cycle launches)");
+  ctx->clear_graphs();
+  ctx->tune[level][mode].by = by;
+  ctx->tune[level][mode].zch = zch;
   return AGCA_OK;
 }
 

@@ -20,6 +20,7 @@ struct DotPairs {
 
 template <int NP>
 __global__ void __launch_bounds__(kRedThreads) dot_partial_kernel(DotPairs p, int64_t n, double* partials) {
+  grid_dep_entry();
   double acc[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) acc[j] = 0.0;
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(kRedThreads) dot_partial_kernel(DotPairs p, in
 
 // one block: out[j] = scale * sum_b partials[j*nb + b], fixed tree order
 __global__ void reduce_final_kernel(const double* partials, int nb, int np, double* out, double scale) {
+  grid_dep_entry();
   __shared__ double red[256];
   for (int j = 0; j < np; ++j) {
     double v = 0.0;
@@ -62,6 +64,7 @@ __global__ void reduce_final_kernel(const double* partials, int nb, int np, doub
 }
 
 __global__ void sum_partial_kernel(const double* x, int64_t n, double* partials) {
+  grid_dep_entry();
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     acc += x[i];
@@ -83,6 +86,7 @@ __global__ void sum_partial_kernel(const double* x, int64_t n, double* partials)
 // round trip; the Lanczos vector z is kept unnormalized (z = gamma zhat).
 __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const double* __restrict__ v,
                                double* vold_to_vnew, const double* __restrict__ sc) {
+  grid_dep_entry();
   if (sc[MS_DONE] != 0.0) return;
   const double g = sc[MS_GAMMA], go = sc[MS_GAMMA_OLD];
   const double ig = 1.0 / g;
@@ -93,6 +97,7 @@ __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const d
 }
 
 __global__ void minres_scalar_kernel(double* sc) {
+  grid_dep_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (sc[MS_DONE] != 0.0) return;
   const double g = sc[MS_GAMMA];
@@ -131,6 +136,7 @@ __global__ void minres_scalar_kernel(double* sc) {
 // w_new = (z/gamma_prev - a3 w_old - a2 w) / a1 into w_old; x += c_new*eta_prev * w_new
 __global__ void minres_update_kernel(int64_t n, const double* __restrict__ z, const double* __restrict__ w,
                                      double* wold_to_wnew, double* x, const double* __restrict__ sc) {
+  grid_dep_entry();
   if (sc[MS_UPD_SKIP] != 0.0) return;
   const double ig = sc[MS_INV_GAMMA_PREV], a1 = sc[MS_A1], a2 = sc[MS_A2], a3 = sc[MS_A3], xc = sc[MS_XCOEF];
   const double ia1 = 1.0 / a1;
@@ -142,6 +148,7 @@ __global__ void minres_update_kernel(int64_t n, const double* __restrict__ z, co
 }
 
 __global__ void minres_init_kernel(double* sc, double tol_rel) {
+  grid_dep_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double g2 = sc[MS_DOT_ZV];
   const double g = g2 > 0.0 ? sqrt(g2) : 0.0;
@@ -160,6 +167,7 @@ __global__ void minres_init_kernel(double* sc, double tol_rel) {
 // ------------------------------------------------------------------ vectors
 __global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
                               const double* scal) {
+  grid_dep_entry();
   const double s0 = scal ? scal[0] : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     switch (op) {
@@ -178,6 +186,7 @@ __global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, con
 
 // --------------------------------------------------------------- FE kernels
 __global__ void load_vector_kernel(int n, const double* __restrict__ fbar, double* __restrict__ b) {
+  grid_dep_entry();
   const int nv = n + 1;
   const int64_t V = nverts(n), E = nelems(n);
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -206,6 +215,7 @@ __global__ void load_vector_kernel(int n, const double* __restrict__ fbar, doubl
 // gradient scaled by h (this is -lambda_e^T (eta_e dA_e/deta_e) u_e).
 __global__ void sensitivity_kernel(int n, const double* __restrict__ eta, const double* __restrict__ lam,
                                    const double* __restrict__ u, double* __restrict__ g) {
+  grid_dep_entry();
   const int nv = n + 1;
   const int64_t V = nverts(n);
   const int64_t cube = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -247,6 +257,7 @@ __global__ void sensitivity_kernel(int n, const double* __restrict__ eta, const 
 }
 
 __global__ void mask_boundary_kernel(int n, double* x) {
+  grid_dep_entry();
   const int nv = n + 1;
   const int64_t V = nverts(n);
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < 3 * V; id += (int64_t)gridDim.x * blockDim.x) {
@@ -261,7 +272,7 @@ inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) /
 }  // namespace
 
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s) {
-  mask_boundary_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x);
+  KL(launch_k(mask_boundary_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, x));
   return cudaGetLastError();
 }
 
@@ -275,57 +286,57 @@ cudaError_t launch_dots(int npairs, const double* const* xs, const double* const
     p.y[j] = ys[j];
   }
   switch (npairs) {
-    case 1: dot_partial_kernel<1><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
-    case 2: dot_partial_kernel<2><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
-    case 3: dot_partial_kernel<3><<<kRedBlocks, kRedThreads, 0, s>>>(p, n, partials); break;
+    case 1: KL(launch_k(dot_partial_kernel<1>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 2: KL(launch_k(dot_partial_kernel<2>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 3: KL(launch_k(dot_partial_kernel<3>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
     default: return cudaErrorInvalidValue;
   }
-  reduce_final_kernel<<<1, 256, 0, s>>>(partials, kRedBlocks, npairs, out, scale);
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, npairs, out, scale));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s) {
-  sum_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partials);
-  reduce_final_kernel<<<1, 256, 0, s>>>(partials, kRedBlocks, 1, out, scale);
+  KL(launch_k(sum_partial_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, x, n, partials));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, 1, out, scale));
   return cudaGetLastError();
 }
 
 cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
                           const double* scal, cudaStream_t s) {
-  vec_op_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(op, n, y, a, b, c, scal);
+  KL(launch_k(vec_op_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, op, n, y, a, b, c, scal));
   return cudaGetLastError();
 }
 
 cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s) {
-  minres_init_kernel<<<1, 32, 0, s>>>(sc, tol_rel);
+  KL(launch_k(minres_init_kernel, dim3(1), dim3(32), 0, s, sc, tol_rel));
   return cudaGetLastError();
 }
 
 cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, const double* sc,
                            cudaStream_t s) {
-  lanczos_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, kz, v, vold_to_vnew, sc);
+  KL(launch_k(lanczos_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, kz, v, vold_to_vnew, sc));
   return cudaGetLastError();
 }
 
 cudaError_t launch_minres_scalars(double* sc, cudaStream_t s) {
-  minres_scalar_kernel<<<1, 32, 0, s>>>(sc);
+  KL(launch_k(minres_scalar_kernel, dim3(1), dim3(32), 0, s, sc));
   return cudaGetLastError();
 }
 
 cudaError_t launch_minres_update(int64_t n, const double* z, const double* w, double* wold_to_wnew, double* x,
                                  const double* sc, cudaStream_t s) {
-  minres_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, z, w, wold_to_wnew, x, sc);
+  KL(launch_k(minres_update_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, z, w, wold_to_wnew, x, sc));
   return cudaGetLastError();
 }
 
 cudaError_t launch_load_vector(int n, const double* fbar, double* b, cudaStream_t s) {
-  load_vector_kernel<<<blocks_for(nverts(n), 128), 128, 0, s>>>(n, fbar, b);
+  KL(launch_k(load_vector_kernel, dim3(blocks_for(nverts(n), 128)), dim3(128), 0, s, n, fbar, b));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
                                cudaStream_t s) {
-  sensitivity_kernel<<<blocks_for((int64_t)n * n * n, 128), 128, 0, s>>>(n, eta, lam, u, g);
+  KL(launch_k(sensitivity_kernel, dim3(blocks_for((int64_t)n * n * n, 128)), dim3(128), 0, s, n, eta, lam, u, g));
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@ namespace agca {
 namespace {
 
 __global__ void check_eta_kernel(const double* eta, int64_t n, int* status) {
+  grid_dep_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = eta[i];
     if (!(isfinite(v) && v > 0.0)) atomicOr(status, 1);
@@ -27,6 +28,7 @@ __device__ __forceinline__ int64_t child_id(const RefineTables& rt, int nf, int 
 __global__ void coarsen_kernel(const RefineTables rt, int nc, const double* __restrict__ mean_f, const double* __restrict__ mx_f,
                                const double* __restrict__ mn_f, double nu, double* __restrict__ mean_c,
                                double* __restrict__ mx_c, double* __restrict__ mn_c, uint8_t* __restrict__ flags) {
+  grid_dep_entry();
   const int64_t E = nelems(nc);
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -55,6 +57,7 @@ __global__ void coarsen_kernel(const RefineTables rt, int nc, const double* __re
 constexpr int kCompactChunk = 1024;  // elements per block (256 threads x 4)
 
 __global__ void compact_count_kernel(const uint8_t* flags, int64_t n, int32_t* counts) {
+  grid_dep_entry();
   const int64_t base = blockIdx.x * (int64_t)kCompactChunk;
   int c = 0;
   for (int i = threadIdx.x; i < kCompactChunk; i += blockDim.x) {
@@ -73,6 +76,7 @@ __global__ void compact_count_kernel(const uint8_t* flags, int64_t n, int32_t* c
 
 // single block: exclusive scan of counts[0..nb) in place, total in *total
 __global__ void compact_scan_kernel(int32_t* counts, int64_t nb, int64_t* total) {
+  grid_dep_entry();
   __shared__ int64_t buf[1024];
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -98,6 +102,7 @@ __global__ void compact_scan_kernel(int32_t* counts, int64_t nb, int64_t* total)
 
 __global__ void compact_scatter_kernel(const uint8_t* flags, int64_t n, const int32_t* offsets, int32_t* fidx,
                                        int32_t* list) {
+  grid_dep_entry();
   const int64_t base = blockIdx.x * (int64_t)kCompactChunk + 4 * threadIdx.x;
   int f[4], c = 0;
 #pragma unroll
@@ -135,6 +140,7 @@ __global__ void compact_scatter_kernel(const uint8_t* flags, int64_t n, const in
 __global__ void galerkin_kernel(const RefineTables rt, int nc, const int32_t* __restrict__ list, int nf, int child_finest,
                                 const double* __restrict__ coef_f, const int32_t* __restrict__ fidx_f,
                                 const double* __restrict__ gca_f, double* __restrict__ gca_c) {
+  grid_dep_entry();
   __shared__ int8_t kp[6][144];
   __shared__ double w[8];
   __shared__ int32_t kf[8];
@@ -182,6 +188,7 @@ __global__ void galerkin_kernel(const RefineTables rt, int nc, const int32_t* __
 }
 
 __global__ void diag_kernel(const LevelOp<double> op, double* diag, double* invD64, float* invD32) {
+  grid_dep_entry();
   const int n = op.n, nv = n + 1;
   const int64_t V = nverts(n);
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -221,6 +228,7 @@ __global__ void diag_kernel(const LevelOp<double> op, double* diag, double* invD
 
 __global__ void gca_to_f32_kernel(int64_t n_flag, const int32_t* list, const double* mx, const double* gca64,
                                   float* gca32, float* scale32) {
+  grid_dep_entry();
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= n_flag * 144) return;
   const int64_t f = id / 144;
@@ -230,16 +238,19 @@ __global__ void gca_to_f32_kernel(int64_t n_flag, const int32_t* list, const dou
 }
 
 __global__ void d2f_kernel(const double* in, float* out, int64_t n) {
+  grid_dep_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
 __global__ void f2d_kernel(const float* in, double* out, int64_t n) {
+  grid_dep_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
 }
 
 // dense level-1 operator on interior DoFs: row (c, iv), col (d, jv)
 __global__ void coarse_assemble_kernel(const LevelOp<double> op, double* dense) {
+  grid_dep_entry();
   const int n = op.n, ni = n - 1;
   const int64_t nI = (int64_t)ni * ni * ni, m = 3 * nI;
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -277,6 +288,7 @@ __global__ void coarse_assemble_kernel(const LevelOp<double> op, double* dense) 
 
 // in-place lower Cholesky of a row-major m x m SPD matrix, one block
 __global__ void cholesky_kernel(double* a, int m, int* status) {
+  grid_dep_entry();
   __shared__ double piv;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int k = 0; k < m; ++k) {
@@ -302,6 +314,7 @@ __global__ void cholesky_kernel(double* a, int m, int* status) {
 
 // X = L^-1 (lower), one thread per column; writes column- and row-major copies
 __global__ void trinv_kernel(const double* l, int m, double* xcm, double* xrm) {
+  grid_dep_entry();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   for (int i = 0; i < j; ++i) {
@@ -323,6 +336,7 @@ __global__ void trinv_kernel(const double* l, int m, double* xcm, double* xrm) {
 template <typename T>
 __global__ void coarse_solve_kernel(int n, const double* __restrict__ xcm, const double* __restrict__ xrm,
                                     const T* __restrict__ r, T* __restrict__ z) {
+  grid_dep_entry();
   extern __shared__ double sm[];
   const int nv = n + 1, ni = n - 1;
   const int64_t V = nverts(n);
@@ -364,6 +378,7 @@ __global__ void coarse_solve_kernel(int n, const double* __restrict__ xcm, const
 }
 
 __global__ void pressure_mass_kernel(const RefineTables rt, int np, const double* __restrict__ eta_f, double* pmass, double* pmass_inv) {
+  grid_dep_entry();
   const int nv = np + 1;
   const int64_t V = nverts(np);
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -395,6 +410,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t idx) {
 }
 
 __global__ void start_vector_kernel(int n, double* v) {
+  grid_dep_entry();
   const int nv = n + 1;
   const int64_t V = nverts(n);
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < 3 * V; id += (int64_t)gridDim.x * blockDim.x) {
@@ -411,14 +427,15 @@ inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) /
 }  // namespace
 
 cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStream_t s) {
-  check_eta_kernel<<<1216, 256, 0, s>>>(eta, n, status);
+  KL(launch_k(check_eta_kernel, dim3(1216), dim3(256), 0, s, eta, n, status));
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarsen(int nc, const double* mean_f, const double* mx_f, const double* mn_f, double nu,
                            double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s) {
   const int64_t E = nelems(nc);
-  coarsen_kernel<<<blocks_for(E, 256), 256, 0, s>>>(refine_tables(), nc, mean_f, mx_f, mn_f, nu, mean_c, mx_c, mn_c, flags);
+  KL(launch_k(coarsen_kernel, dim3(blocks_for(E, 256)), dim3(256), 0, s,
+     refine_tables(), nc, mean_f, mx_f, mn_f, nu, mean_c, mx_c, mn_c, flags));
   return cudaGetLastError();
 }
 
@@ -427,9 +444,9 @@ int64_t compact_scratch_blocks(int64_t n) { return (n + kCompactChunk - 1) / kCo
 cudaError_t launch_compact(const uint8_t* flags, int64_t n, int32_t* fidx, int32_t* list, int32_t* block_counts,
                            int64_t* total, cudaStream_t s) {
   const int64_t nb = compact_scratch_blocks(n);
-  compact_count_kernel<<<(unsigned)nb, 256, 0, s>>>(flags, n, block_counts);
-  compact_scan_kernel<<<1, 1024, 0, s>>>(block_counts, nb, total);
-  compact_scatter_kernel<<<(unsigned)nb, 256, 0, s>>>(flags, n, block_counts, fidx, list);
+  KL(launch_k(compact_count_kernel, dim3((unsigned)nb), dim3(256), 0, s, flags, n, block_counts));
+  KL(launch_k(compact_scan_kernel, dim3(1), dim3(1024), 0, s, block_counts, nb, total));
+  KL(launch_k(compact_scatter_kernel, dim3((unsigned)nb), dim3(256), 0, s, flags, n, block_counts, fidx, list));
   return cudaGetLastError();
 }
 
@@ -437,45 +454,47 @@ cudaError_t launch_galerkin(int nc, int64_t n_flag, const int32_t* list, int nf,
                             const double* coef_f, const int32_t* fidx_f, const double* gca_f, double* gca_c,
                             cudaStream_t s) {
   if (n_flag == 0) return cudaSuccess;
-  galerkin_kernel<<<(unsigned)n_flag, 160, 0, s>>>(refine_tables(), nc, list, nf, child_finest ? 1 : 0, coef_f, fidx_f, gca_f, gca_c);
+  KL(launch_k(galerkin_kernel, dim3((unsigned)n_flag), dim3(160), 0, s,
+     refine_tables(), nc, list, nf, child_finest ? 1 : 0, coef_f, fidx_f, gca_f, gca_c));
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const LevelOp<double>& op, double* diag, double* invD64, float* invD32, cudaStream_t s) {
   const int64_t V = nverts(op.n);
-  diag_kernel<<<blocks_for(V, 128), 128, 0, s>>>(op, diag, invD64, invD32);
+  KL(launch_k(diag_kernel, dim3(blocks_for(V, 128)), dim3(128), 0, s, op, diag, invD64, invD32));
   return cudaGetLastError();
 }
 
 cudaError_t launch_gca_to_f32(int64_t n_flag, const int32_t* list, const double* mx, const double* gca64,
                               float* gca32, float* scale32, cudaStream_t s) {
   if (n_flag == 0) return cudaSuccess;
-  gca_to_f32_kernel<<<blocks_for(n_flag * 144, 256), 256, 0, s>>>(n_flag, list, mx, gca64, gca32, scale32);
+  KL(launch_k(gca_to_f32_kernel, dim3(blocks_for(n_flag * 144, 256)), dim3(256), 0, s,
+     n_flag, list, mx, gca64, gca32, scale32));
   return cudaGetLastError();
 }
 
 cudaError_t launch_d2f(const double* in, float* out, int64_t n, cudaStream_t s) {
-  d2f_kernel<<<1216, 256, 0, s>>>(in, out, n);
+  KL(launch_k(d2f_kernel, dim3(1216), dim3(256), 0, s, in, out, n));
   return cudaGetLastError();
 }
 cudaError_t launch_f2d(const float* in, double* out, int64_t n, cudaStream_t s) {
-  f2d_kernel<<<1216, 256, 0, s>>>(in, out, n);
+  KL(launch_k(f2d_kernel, dim3(1216), dim3(256), 0, s, in, out, n));
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_assemble(const LevelOp<double>& op, double* dense, cudaStream_t s) {
   const int64_t ni = op.n - 1, m = 3 * ni * ni * ni;
-  coarse_assemble_kernel<<<blocks_for(m * m, 128), 128, 0, s>>>(op, dense);
+  KL(launch_k(coarse_assemble_kernel, dim3(blocks_for(m * m, 128)), dim3(128), 0, s, op, dense));
   return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky(double* a, int m, int* status, cudaStream_t s) {
-  cholesky_kernel<<<1, 1024, 0, s>>>(a, m, status);
+  KL(launch_k(cholesky_kernel, dim3(1), dim3(1024), 0, s, a, m, status));
   return cudaGetLastError();
 }
 
 cudaError_t launch_trinv(const double* l, int m, double* linv_cm, double* linv_rm, cudaStream_t s) {
-  trinv_kernel<<<blocks_for(m, 64), 64, 0, s>>>(l, m, linv_cm, linv_rm);
+  KL(launch_k(trinv_kernel, dim3(blocks_for(m, 64)), dim3(64), 0, s, l, m, linv_cm, linv_rm));
   return cudaGetLastError();
 }
 
@@ -484,7 +503,7 @@ cudaError_t launch_coarse_solve(int n, const double* linv_cm, const double* linv
                                 cudaStream_t s) {
   const int ni = n - 1, m = 3 * ni * ni * ni;
   const size_t smem = 2 * (size_t)m * sizeof(double);
-  coarse_solve_kernel<T><<<1, 1024, smem, s>>>(n, linv_cm, linv_rm, r, z);
+  KL(launch_k(coarse_solve_kernel<T>, dim3(1), dim3(1024), smem, s, n, linv_cm, linv_rm, r, z));
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(int, const double*, const double*, const float*, float*, cudaStream_t);
@@ -493,12 +512,13 @@ template cudaError_t launch_coarse_solve<double>(int, const double*, const doubl
 
 cudaError_t launch_pressure_mass(int np, const double* eta_f, double* pmass, double* pmass_inv, cudaStream_t s) {
   const int64_t V = nverts(np);
-  pressure_mass_kernel<<<blocks_for(V, 128), 128, 0, s>>>(refine_tables(), np, eta_f, pmass, pmass_inv);
+  KL(launch_k(pressure_mass_kernel, dim3(blocks_for(V, 128)), dim3(128), 0, s,
+     refine_tables(), np, eta_f, pmass, pmass_inv));
   return cudaGetLastError();
 }
 
 cudaError_t launch_start_vector(int n, double* v, cudaStream_t s) {
-  start_vector_kernel<<<1216, 256, 0, s>>>(n, v);
+  KL(launch_k(start_vector_kernel, dim3(1216), dim3(256), 0, s, n, v));
   return cudaGetLastError();
 }
 

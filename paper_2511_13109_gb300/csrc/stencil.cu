@@ -147,12 +147,17 @@ __host__ __device__ constexpr size_t stencil_smem_bytes() {
          (size_t)2 * NC * BX * BY * sizeof(T);
 }
 
-// One CTA tile (bx, by, bz) of the stencil; called by the single-operator
-// kernel (tile = block index) and by the persistent batched kernel.
+// One CTA tile of the stencil: vertex columns x0.. and rows y0.. (origin of
+// the owned (BX-1) x (BY-1) block), z-chunk bz; thread (tx, ty) with
+// tid = ty * BX + tx, so a warp spans 32 / BX rows of the tile (BX = 32 or 8;
+// the shuffle along x then crosses rows only into the non-owning last
+// column).  Called by the single-operator kernel and by the persistent
+// batched kernel.
 template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
 __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const StencilArgs<TS>& a, const int zch,
-                                              const int bx, const int by, const int bz,
+                                              const int x0, const int y0, const int bz, const int tx, const int ty,
                                               unsigned char* __restrict__ smem_raw) {
+  static_assert(BX == 32 || BX == 8, "a tile row is a whole warp or a quarter of one");
   constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;  // combined fields: velocity (+ divergence)
   constexpr int NF = stencil_tile_fields<MODE, TS>();
   constexpr int TW = BX + 1, TSZ = (BX + 1) * (BY + 1), NT = BX * BY;
@@ -165,9 +170,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   const int nv = n + 1;
   const int64_t V = (int64_t)nv * nv * nv;
   const int64_t plane = (int64_t)nv * nv;
-  const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
-  const int x0 = bx * (BX - 1), y0 = by * (BY - 1);
   const int z0 = bz * zch;
   const int z1 = min(z0 + zch, nv);
   const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
@@ -396,7 +399,10 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
               o = xo + a.s0 * xo + a.s1 * ed[c] * (eb[c] - y);
             }
           }
-          a.out[i] = o;
+          if (MODE != ST_STOKES && a.out64)
+            a.out64[i] = (double)o;
+          else
+            a.out[i] = o;
         }
         if (MODE == ST_STOKES) a.out2[vo] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
       }
@@ -413,11 +419,29 @@ __host__ __device__ constexpr int stencil_min_blocks() {
   return sizeof(T) == 4 ? (BY <= 8 ? 3 : (BY <= 12 ? 2 : 1)) : 2;
 }
 
-template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
-__global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
-    stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch) {
+// Single-operator launch over two tile classes: wide tiles (32 x BY threads,
+// 31 x (BY-1) owned vertices) cover the first gxw * 31 vertex columns, narrow
+// tiles (8 x 4BY threads, 7 x (4BY-1) owned) the columns x0n.. left over.
+// A vertex row of n+1 = 129 columns is then 4 wide + 1 narrow strip instead
+// of 5 wide strips whose last one would keep 26 of 32 lanes idle.  Both
+// classes have 32 * BY threads and the same shared-memory layout size class.
+template <typename TS, typename T, int BY, int MODE, bool COARSE>
+__global__ void __launch_bounds__(32 * BY, stencil_min_blocks<T, BY>())
+    stencil_kernel(const LevelOp<T> op, const StencilArgs<TS> a, const int zch, const int gxw, const int gyw,
+                   const int gxn, const int x0n) {
+  grid_dep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stencil_block<TS, T, BX, BY, MODE, COARSE>(op, a, zch, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  const int tid = threadIdx.x;
+  const int t = blockIdx.x, nw = gxw * gyw;
+  if (t < nw) {
+    stencil_block<TS, T, 32, BY, MODE, COARSE>(op, a, zch, (t % gxw) * 31, (t / gxw) * (BY - 1), blockIdx.y,
+                                               tid & 31, tid >> 5, smem_raw);
+  } else {
+    constexpr int BYN = 4 * BY;
+    const int u = t - nw;
+    stencil_block<TS, T, 8, BYN, MODE, COARSE>(op, a, zch, x0n + (u % gxn) * 7, (u / gxn) * (BYN - 1), blockIdx.y,
+                                               tid & 7, tid >> 3, smem_raw);
+  }
 }
 
 // Persistent batched form: one launch applies the same stencil mode to many
@@ -426,6 +450,7 @@ __global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
 template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
 __global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
     stencil_batch_kernel(const StencilTask<TS, T>* __restrict__ tasks, const int ntasks, const int64_t ntiles) {
+  grid_dep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
     int j = 0;
@@ -434,7 +459,8 @@ __global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
     if (tk.sc && tk.sc[MS_DONE] != 0.0) continue;  // converged problem
     const int64_t local = it - tk.tile0;
     const int bx = (int)(local % tk.gx), by = (int)((local / tk.gx) % tk.gy), bz = (int)(local / ((int64_t)tk.gx * tk.gy));
-    stencil_block<TS, T, BX, BY, MODE, COARSE>(tk.op, tk.a, tk.zch, bx, by, bz, smem_raw);
+    stencil_block<TS, T, BX, BY, MODE, COARSE>(tk.op, tk.a, tk.zch, bx * (BX - 1), by * (BY - 1), bz, threadIdx.x,
+                                               threadIdx.y, smem_raw);
     __syncthreads();  // the shared-memory rings are reused by the next tile
   }
 }
@@ -443,7 +469,9 @@ __global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
 // Flagged elements of a coarse level: y_e = s_e A_e x_e (Eq. 2.9, stored
 // Galerkin part), one thread per (element, row), written to op.ye for the
 // stencil kernel to scatter.  x follows the stencil's input convention
-// (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).
+// (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).  A separate
+// launch spreads the clustered flagged elements over the whole GPU; inside
+// the stencil they would serialise in the few warps whose cubes hold them.
 template <typename TS, typename T, bool PRE>
 __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
   const int64_t f = id / 12;
@@ -479,6 +507,7 @@ __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<
 
 template <typename TS, typename T, bool PRE>
 __global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
+  grid_dep_entry();
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= op.n_flag * 12) return;
   gca_row<TS, T, PRE>(op, a, id);
@@ -486,6 +515,7 @@ __global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {
 
 template <typename TS, typename T, bool PRE>
 __global__ void gca_apply_batch_kernel(const StencilTask<TS, T>* __restrict__ tasks) {
+  grid_dep_entry();
   const StencilTask<TS, T>& tk = tasks[blockIdx.y];
   if (tk.sc && tk.sc[MS_DONE] != 0.0) return;
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -493,33 +523,33 @@ __global__ void gca_apply_batch_kernel(const StencilTask<TS, T>* __restrict__ ta
   gca_row<TS, T, PRE>(tk.op, tk.a, id);
 }
 
-template <typename TS, typename T, int BX, int BY, bool COARSE>
+template <typename TS, typename T, int BY, bool COARSE>
 cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s, int zch_req) {
-  int gx, gy, gz, zch;
-  stencil_grid_by(op.n, BY, zch_req, &gx, &gy, &gz, &zch);
+  const TileGrid tg = stencil_tiles(op.n, BY, zch_req);
   if (COARSE && op.n_flag > 0) {
-    const int64_t nth = op.n_flag * 12;
-    const unsigned gb = (unsigned)((nth + 127) / 128);
+    const unsigned gb = (unsigned)((op.n_flag * 12 + 127) / 128);
     if (mode == ST_CHEB_PRE)
-      gca_apply_kernel<TS, T, true><<<gb, 128, 0, s>>>(op, a);
+      KL(launch_k(gca_apply_kernel<TS, T, true>, dim3(gb), dim3(128), 0, s, op, a));
     else
-      gca_apply_kernel<TS, T, false><<<gb, 128, 0, s>>>(op, a);
+      KL(launch_k(gca_apply_kernel<TS, T, false>, dim3(gb), dim3(128), 0, s, op, a));
   }
-  dim3 grid(gx, gy, gz), block(BX, BY);
+  const dim3 grid((unsigned)tg.per_z(), (unsigned)tg.gz), block(32 * BY);
 #define AGCA_LAUNCH(M, C)                                                                                  \
   do {                                                                                                     \
-    constexpr size_t smem = stencil_smem_bytes<TS, T, BX, BY, M>();                                       \
+    constexpr size_t smem = std::max(stencil_smem_bytes<TS, T, 32, BY, M>(),                              \
+                                     stencil_smem_bytes<TS, T, 8, 4 * BY, M>());                          \
     static bool attr_set[64] = {};                                                                        \
     int dev_ = 0;                                                                                         \
     cudaError_t e = cudaGetDevice(&dev_);                                                                 \
     if (e != cudaSuccess) return e;                                                                       \
     if (smem > 48 * 1024 && dev_ >= 0 && dev_ < 64 && !attr_set[dev_]) {                                  \
-      e = cudaFuncSetAttribute(stencil_kernel<TS, T, BX, BY, M, C>,                                       \
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
+      e = cudaFuncSetAttribute(stencil_kernel<TS, T, BY, M, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)smem);                                                                \
       if (e != cudaSuccess) return e;                                                                     \
       attr_set[dev_] = true;                                                                              \
     }                                                                                                     \
-    stencil_kernel<TS, T, BX, BY, M, C><<<grid, block, smem, s>>>(op, a, zch);                            \
+    KL(launch_k(stencil_kernel<TS, T, BY, M, C>, grid, block, smem, s, op, a, tg.zch, tg.gxw, tg.gyw, tg.gxn, \
+                tg.x0n));                                                                                 \
   } while (0)
   switch (mode) {
     case ST_APPLY: AGCA_LAUNCH(ST_APPLY, COARSE); break;
@@ -545,11 +575,11 @@ cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int nta
                               int64_t max_gca_rows, cudaStream_t s) {
   if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
   if (COARSE && max_gca_rows > 0) {
-    dim3 g((unsigned)((max_gca_rows + 127) / 128), (unsigned)ntasks);
+    const dim3 g((unsigned)((max_gca_rows + 127) / 128), (unsigned)ntasks);
     if (mode == ST_CHEB_PRE)
-      gca_apply_batch_kernel<TS, T, true><<<g, 128, 0, s>>>(tasks);
+      KL(launch_k(gca_apply_batch_kernel<TS, T, true>, g, dim3(128), 0, s, tasks));
     else
-      gca_apply_batch_kernel<TS, T, false><<<g, 128, 0, s>>>(tasks);
+      KL(launch_k(gca_apply_batch_kernel<TS, T, false>, g, dim3(128), 0, s, tasks));
   }
   int dev = 0, sms = 152;
   cudaError_t e = cudaGetDevice(&dev);
@@ -569,7 +599,7 @@ cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int nta
       if (e != cudaSuccess) return e;                                                                     \
       attr_set[dev] = true;                                                                               \
     }                                                                                                     \
-    stencil_batch_kernel<TS, T, BX, BY, M, C><<<grid, block, smem, s>>>(tasks, ntasks, ntiles);  \
+    KL(launch_k(stencil_batch_kernel<TS, T, BX, BY, M, C>, grid, block, smem, s, tasks, ntasks, ntiles)); \
   } while (0)
   switch (mode) {
     case ST_RESID: AGCA_BLAUNCH(ST_RESID, COARSE); break;
@@ -613,6 +643,37 @@ void stencil_grid_by(int n, int BY, int zch_req, int* gx_out, int* gy_out, int* 
   *zch_out = zch;
 }
 
+TileGrid stencil_tiles(int n, int BY, int zch_req) {
+  const int nv = n + 1;
+  const int BYN = 4 * BY;
+  TileGrid g;
+  g.gyw = (nv + BY - 2) / (BY - 1);
+  g.gyn = (nv + BYN - 2) / (BYN - 1);
+  // strips of 31 columns (wide) while they are full, the rest in strips of
+  // 7 (narrow) if that takes fewer blocks than one more wide strip
+  const int full = nv / 31, rem = nv - 31 * full;
+  const int nar = (rem + 6) / 7;
+  if (rem == 0 || nar * g.gyn < g.gyw) {
+    g.gxw = full;
+    g.gxn = nar;
+  } else {
+    g.gxw = full + 1;
+    g.gxn = 0;
+  }
+  g.x0n = 31 * g.gxw;
+  if (g.gxn == 0) g.gyn = 0;
+  const int per = g.per_z();
+  // default: enough blocks for two waves of 3 resident 256-thread blocks per
+  // SM (as stencil_grid_by); zch_req > 0 (autotuner) overrides
+  int gz = (912 * 8 / BY + per - 1) / per;
+  int zch = zch_req > 0 ? zch_req : (nv + gz - 1) / gz;
+  if (zch < 1) zch = 1;
+  if (zch > nv) zch = nv;
+  g.gz = (nv + zch - 1) / zch;
+  g.zch = zch;
+  return g;
+}
+
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s) {
@@ -632,17 +693,17 @@ cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>
   const int by = cfg ? cfg->by : 8, zch = cfg ? cfg->zch : 0;
   if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
     if (by == 12) {
-      if (op.fidx) return launch_mode<TS, T, 32, 12, true>(mode, op, a, s, zch);
-      return launch_mode<TS, T, 32, 12, false>(mode, op, a, s, zch);
+      if (op.fidx) return launch_mode<TS, T, 12, true>(mode, op, a, s, zch);
+      return launch_mode<TS, T, 12, false>(mode, op, a, s, zch);
     }
     if (by == 16) {
-      if (op.fidx) return launch_mode<TS, T, 32, 16, true>(mode, op, a, s, zch);
-      return launch_mode<TS, T, 32, 16, false>(mode, op, a, s, zch);
+      if (op.fidx) return launch_mode<TS, T, 16, true>(mode, op, a, s, zch);
+      return launch_mode<TS, T, 16, false>(mode, op, a, s, zch);
     }
   }
-  if (by != 8) return cudaErrorInvalidValue;
-  if (op.fidx) return launch_mode<TS, T, 32, 8, true>(mode, op, a, s, zch);
-  return launch_mode<TS, T, 32, 8, false>(mode, op, a, s, zch);
+  // 8 block rows otherwise (a tile shape never changes the result)
+  if (op.fidx) return launch_mode<TS, T, 8, true>(mode, op, a, s, zch);
+  return launch_mode<TS, T, 8, false>(mode, op, a, s, zch);
 }
 
 template cudaError_t launch_stencil<float, float>(int, const LevelOp<float>&, const StencilArgs<float>&,

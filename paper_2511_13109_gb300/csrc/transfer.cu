@@ -7,6 +7,8 @@
 //   (P e)(2i) = e(i),  (P e)(2i + d) = (e(i) + e(i + d)) / 2,
 //   (P^T r)(i) = r(2i) + 1/2 sum_d [ r(2i + d) + r(2i - d) ].
 // The weights are known a priori and never stored.
+#include <stdlib.h>
+
 #include "agca_internal.cuh"
 
 namespace agca {
@@ -15,6 +17,7 @@ namespace {
 
 template <typename T>
 __global__ void restrict_kernel(int nf, int ncomp, bool mask, T scale, const T* __restrict__ rf, T* __restrict__ rc) {
+  grid_dep_entry();
   const int nc = nf / 2;
   const int nvf = nf + 1, nvc = nc + 1;
   const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
@@ -44,6 +47,7 @@ __global__ void restrict_kernel(int nf, int ncomp, bool mask, T scale, const T* 
 
 template <typename T, bool ADD>
 __global__ void prolong_kernel(int nf, int ncomp, bool mask, const T* __restrict__ ec, T* __restrict__ xf) {
+  grid_dep_entry();
   const int nc = nf / 2;
   const int nvf = nf + 1, nvc = nc + 1;
   const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
@@ -68,11 +72,20 @@ __global__ void prolong_kernel(int nf, int ncomp, bool mask, const T* __restrict
 
 }  // namespace
 
+bool pdl_enabled(cudaStream_t s) {
+  static const bool on = [] {
+    const char* v = getenv("AGCA_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on && s != nullptr && s != cudaStreamLegacy;
+}
+
 template <typename T>
 cudaError_t launch_restrict(int nf, int ncomp, bool mask, T scale, const T* rf, T* rc, cudaStream_t s) {
   const int64_t Vc = nverts(nf / 2);
   const int bs = 256;
-  restrict_kernel<T><<<(unsigned)((Vc + bs - 1) / bs), bs, 0, s>>>(nf, ncomp, mask, scale, rf, rc);
+  KL(launch_k(restrict_kernel<T>, dim3((unsigned)((Vc + bs - 1) / bs)), dim3(bs), 0, s,
+     nf, ncomp, mask, scale, rf, rc));
   return cudaGetLastError();
 }
 
@@ -82,9 +95,9 @@ cudaError_t launch_prolong(int nf, int ncomp, bool mask, bool add, const T* ec, 
   const int bs = 256;
   const unsigned g = (unsigned)((Vf + bs - 1) / bs);
   if (add)
-    prolong_kernel<T, true><<<g, bs, 0, s>>>(nf, ncomp, mask, ec, xf);
+    KL(launch_k(prolong_kernel<T, true>, dim3(g), dim3(bs), 0, s, nf, ncomp, mask, ec, xf));
   else
-    prolong_kernel<T, false><<<g, bs, 0, s>>>(nf, ncomp, mask, ec, xf);
+    KL(launch_k(prolong_kernel<T, false>, dim3(g), dim3(bs), 0, s, nf, ncomp, mask, ec, xf));
   return cudaGetLastError();
 }
 

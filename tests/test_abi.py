@@ -58,6 +58,12 @@ def test_host_only_calls(libagca):
     assert L.agca_set_solver_options(h, 0.0, 4) == 1
     assert L.agca_set_solver_options(h, 1e-4, 0) == 1
     assert L.agca_set_solver_options(h, 1e-4, 8) == 0
+    assert L.agca_set_tile_config(h, 2, 1, 8, 5) == 0
+    assert L.agca_set_tile_config(h, 2, 1, 12, 0) == 1   # 12 block rows: FP32 cycle launches only
+    assert L.agca_set_tile_config(h, 0, 1, 8, 0) == 1
+    assert L.agca_set_tile_config(h, 2, 6, 8, 0) == 1
+    by, zc = ctypes.c_int(), ctypes.c_int()
+    assert L.agca_tile_config(h, 2, 1, ctypes.byref(by), ctypes.byref(zc)) == 0 and (by.value, zc.value) == (8, 5)
     L.agca_destroy(h)
     bad = ctypes.c_void_p()
     assert L.agca_create(16, 6, 0, None, ctypes.byref(bad)) == 1   # 32 cubes cannot coarsen 5 times to >= 2
