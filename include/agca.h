@@ -87,8 +87,8 @@ typedef struct {
 const char* agca_status_string(agca_status s);
 
 /* Create a context for a velocity grid of 2N cubes per axis with n_levels
- * levels (2N must be divisible by 2^(n_levels-1) with at least 2 cubes per
- * axis on level 1).  prec selects the V-cycle precision: AGCA_FP64, or
+ * levels (1 <= N <= 256; 2N must be divisible by 2^(n_levels-1) with at
+ * least 2 cubes per axis on level 1).  prec selects the V-cycle precision: AGCA_FP64, or
  * AGCA_MIXED (FP32 smoothing, transfers and coarse applies; FP64 Galerkin
  * assembly, coarsest solve and Krylov recurrence).  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  Host-only; *out is owned by

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "agca_internal.cuh"
+#include "device_ops.cuh"
 
 namespace agca {
 
@@ -23,32 +24,15 @@ __global__ void restrict_batch_kernel(const XferTask* __restrict__ tasks) {
   grid_dep_entry();
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
-  const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
+  const int nf = tk.nf, nvf = nf + 1, nvc = nf / 2 + 1;
   const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= Vc) return;
   const T* rf = static_cast<const T*>(tk.src);
   T* rc = static_cast<T*>(tk.dst);
   const int I = (int)(id % nvc), J = (int)((id / nvc) % nvc), K = (int)(id / ((int64_t)nvc * nvc));
-  const bool bd = I == 0 || J == 0 || K == 0 || I == nc || J == nc || K == nc;
-  for (int c = 0; c < tk.ncomp; ++c) {
-    T out = T(0);
-    if (!(tk.mask && bd)) {
-      const T* r = rf + c * Vf;
-      const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
-      T acc = T(0);
-#pragma unroll
-      for (int d = 1; d < 8; ++d) {
-        const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
-        if (fi + dx <= nf && fj + dy <= nf && fk + dz <= nf)
-          acc += r[(fi + dx) + (int64_t)nvf * ((fj + dy) + (int64_t)nvf * (fk + dz))];
-        if (fi - dx >= 0 && fj - dy >= 0 && fk - dz >= 0)
-          acc += r[(fi - dx) + (int64_t)nvf * ((fj - dy) + (int64_t)nvf * (fk - dz))];
-      }
-      out = (T)tk.scale * (r[fi + (int64_t)nvf * (fj + (int64_t)nvf * fk)] + T(0.5) * acc);
-    }
-    rc[c * Vc + id] = out;
-  }
+  for (int c = 0; c < tk.ncomp; ++c)
+    rc[c * Vc + id] = restrict_point<T>(nf, tk.mask, (T)tk.scale, rf + c * Vf, I, J, K);
 }
 
 template <typename T, bool ADD>
@@ -56,22 +40,15 @@ __global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
   grid_dep_entry();
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
-  const int nf = tk.nf, nc = nf / 2, nvf = nf + 1, nvc = nc + 1;
+  const int nf = tk.nf, nvf = nf + 1, nvc = nf / 2 + 1;
   const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= Vf) return;
   const T* ec = static_cast<const T*>(tk.src);
   T* xf = static_cast<T*>(tk.dst);
   const int i = (int)(id % nvf), j = (int)((id / nvf) % nvf), k = (int)(id / ((int64_t)nvf * nvf));
-  const bool bd = i == 0 || j == 0 || k == 0 || i == nf || j == nf || k == nf;
-  const int I = i >> 1, J = j >> 1, K = k >> 1, dx = i & 1, dy = j & 1, dz = k & 1;
-  const int64_t c0 = I + (int64_t)nvc * (J + (int64_t)nvc * K);
-  const int64_t c1 = (I + dx) + (int64_t)nvc * ((J + dy) + (int64_t)nvc * (K + dz));
-  const bool odd = dx | dy | dz;
   for (int c = 0; c < tk.ncomp; ++c) {
-    const T* e = ec + c * Vc;
-    T v = odd ? T(0.5) * (e[c0] + e[c1]) : e[c0];
-    if (tk.mask && bd) v = T(0);
+    const T v = prolong_point<T>(nf, tk.mask, ec + c * Vc, i, j, k);
     if (ADD)
       xf[c * Vf + id] += v;
     else
@@ -90,54 +67,14 @@ __global__ void convert_batch_kernel(const XferTask* __restrict__ tasks) {
     out[i] = (TO)in[i];
 }
 
-// coarsest solves, one block per problem (as coarse_solve_kernel)
+// coarsest solves, one block per problem
 template <typename T>
 __global__ void coarse_solve_batch_kernel(const XferTask* __restrict__ tasks) {
   grid_dep_entry();
   extern __shared__ double sm[];
   const XferTask tk = tasks[blockIdx.x];
   if (skip(tk.sc)) return;
-  const int n = tk.nf, nv = n + 1, ni = n - 1;
-  const int64_t V = nverts(n);
-  const int nI = ni * ni * ni, m = 3 * nI;
-  const double* xcm = tk.m1;
-  const double* xrm = tk.m2;
-  const T* r = static_cast<const T*>(tk.src);
-  T* z = static_cast<T*>(tk.dst);
-  double* rs = sm;
-  double* ts = sm + m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
-    const int c = q / nI, iv = q % nI;
-    const int i = 1 + iv % ni, j = 1 + (iv / ni) % ni, k = 1 + iv / (ni * ni);
-    rs[q] = (double)r[c * V + i + (int64_t)nv * (j + (int64_t)nv * k)];
-  }
-  __syncthreads();
-  for (int q = warp; q < m; q += nw) {
-    double s = 0.0;
-    for (int p = lane; p <= q; p += 32) s = fma(xrm[(int64_t)q * m + p], rs[p], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) ts[q] = s;
-  }
-  __syncthreads();
-  for (int q = warp; q < m; q += nw) {
-    double s = 0.0;
-    for (int p = q + lane; p < m; p += 32) s = fma(xcm[(int64_t)q * m + p], ts[p], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) rs[q] = s;
-  }
-  __syncthreads();
-  for (int64_t id = threadIdx.x; id < 3 * V; id += blockDim.x) {
-    const int c = (int)(id / V);
-    const int64_t v = id % V;
-    const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
-    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
-    T out = T(0);
-    if (inner) out = (T)rs[c * nI + (i - 1) + ni * ((j - 1) + ni * (k - 1))];
-    z[id] = out;
-  }
+  coarse_solve_block<T>(tk.nf, tk.m1, tk.m2, static_cast<const T*>(tk.src), static_cast<T*>(tk.dst), sm);
 }
 
 // ------------------------------------------------------------------ Krylov

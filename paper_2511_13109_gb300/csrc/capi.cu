@@ -1120,7 +1120,10 @@ const char* agca_status_string(agca_status s) {
 agca_status agca_create(int N, int n_levels, int prec, void* cuda_stream, agca_ctx** out) {
   if (!out) return AGCA_EINVAL;
   *out = nullptr;
-  if (N < 1 || n_levels < 2 || n_levels > 12 || (prec != AGCA_FP64 && prec != AGCA_MIXED)) return AGCA_EINVAL;
+  // N <= 256 keeps every per-level index below 2^31 (3 (2N+1)^3 vertex entries,
+  // 6 (2N)^3 elements): the kernels index with 32-bit integers
+  if (N < 1 || N > 256 || n_levels < 2 || n_levels > 12 || (prec != AGCA_FP64 && prec != AGCA_MIXED))
+    return AGCA_EINVAL;
   const int nL = 2 * N;
   if (nL % (1 << (n_levels - 1)) != 0 || (nL >> (n_levels - 1)) < 2) return AGCA_EINVAL;
   if (nL > 1024) return AGCA_EINVAL;

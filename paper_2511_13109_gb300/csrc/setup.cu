@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "agca_internal.cuh"
+#include "device_ops.cuh"
 
 namespace agca {
 
@@ -331,50 +332,12 @@ __global__ void trinv_kernel(const double* l, int m, double* xcm, double* xrm) {
 }
 
 // z = L^-T L^-1 r on the interior DoFs of level 1, one block; r, z full-grid.
-// One warp per row of each triangular product with coalesced row reads
-// (X row-major for t = X r, X column-major for z = X^T t).
 template <typename T>
 __global__ void coarse_solve_kernel(int n, const double* __restrict__ xcm, const double* __restrict__ xrm,
                                     const T* __restrict__ r, T* __restrict__ z) {
   grid_dep_entry();
   extern __shared__ double sm[];
-  const int nv = n + 1, ni = n - 1;
-  const int64_t V = nverts(n);
-  const int nI = ni * ni * ni, m = 3 * nI;
-  double* rs = sm;
-  double* ts = sm + m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
-    const int c = q / nI, iv = q % nI;
-    const int i = 1 + iv % ni, j = 1 + (iv / ni) % ni, k = 1 + iv / (ni * ni);
-    rs[q] = (double)r[c * V + i + (int64_t)nv * (j + (int64_t)nv * k)];
-  }
-  __syncthreads();
-  for (int q = warp; q < m; q += nw) {
-    double s = 0.0;
-    for (int p = lane; p <= q; p += 32) s = fma(xrm[(int64_t)q * m + p], rs[p], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) ts[q] = s;
-  }
-  __syncthreads();
-  for (int q = warp; q < m; q += nw) {
-    double s = 0.0;
-    for (int p = q + lane; p < m; p += 32) s = fma(xcm[(int64_t)q * m + p], ts[p], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) rs[q] = s;
-  }
-  __syncthreads();
-  for (int64_t id = threadIdx.x; id < 3 * V; id += blockDim.x) {
-    const int c = (int)(id / V);
-    const int64_t v = id % V;
-    const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
-    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
-    T out = T(0);
-    if (inner) out = (T)rs[c * nI + (i - 1) + ni * ((j - 1) + ni * (k - 1))];
-    z[id] = out;
-  }
+  coarse_solve_block<T>(n, xcm, xrm, r, z, sm);
 }
 
 __global__ void pressure_mass_kernel(const RefineTables rt, int np, const double* __restrict__ eta_f, double* pmass, double* pmass_inv) {

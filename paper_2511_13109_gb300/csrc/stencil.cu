@@ -1,15 +1,7 @@
 // Matrix-free operator application on a Kuhn cube grid, fused with the
 // smoother and residual epilogues (Eq. 2.3 on the finest level, the
-// heterogeneous AGCA operator of Eq. 2.9 on coarse levels).
-//
-// Element action.  For a tetrahedron with nodal values x_a (a = 0..3) the
-// scaled displacement gradient is Gx = sum_a x_a (x) G_a; along the Kuhn path
-// its column p_k is the edge difference x_{k+1} - x_k.  With S = Gx + Gx^T,
-// the element contribution to local vertex a is y_a = eta (h/6) S G_a, i.e.
-// with the edge "fluxes" F_k = eta (h/6) S[:, p_k]:
-//   y_0 = -F_0, y_1 = F_0 - F_1, y_2 = F_1 - F_2, y_3 = F_2.
-// This equals A_e x_e for the element matrix of Eq. 3.5 and needs only
-// differences of nodal values.
+// heterogeneous AGCA operator of Eq. 2.9 on coarse levels); the per-cube
+// element action (cube_dca) is in device_ops.cuh.
 //
 // Tiling (GB300): a CTA of BX x BY threads owns a (BX-1) x (BY-1) column of
 // vertices and marches through a chunk of z-planes.  Thread (tx, ty) computes
@@ -20,98 +12,20 @@
 // each owner finishes its vertex in registers (owner-computes: no atomics,
 // deterministic summation order).  HBM traffic per vertex is one read of x,
 // the 6 element coefficients and the epilogue vectors, and one write.
+//
+// Summation order at vertex (i, j, k), Y(cube)[corner] the cube's corner sums
+// (zero for cubes outside the grid):
+//   [(Y(i-1,j-1,k-1)[7] + Y(i,j-1,k-1)[6]) + (Y(i-1,j,k-1)[5] + Y(i,j,k-1)[4])]
+//   + [(Y(i-1,j-1,k)[3] + Y(i,j-1,k)[2]) + (Y(i-1,j,k)[1] + Y(i,j,k)[0])]
+// whatever the tile shape (results do not depend on it).
 #include <algorithm>
 
 #include "agca_internal.cuh"
+#include "device_ops.cuh"
 
 namespace agca {
 
 namespace {
-
-template <typename T, int NC>
-__device__ __forceinline__ void cube_dca(const T (&Xl)[4][NC], const T (&Xh)[4][NC], const T (&c)[6], T (&Y)[8][NC]) {
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    T G[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int qa = tet_corner(t, k), qb = tet_corner(t, k + 1), m = perm(t, k);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T xb = (qb & 4) ? Xh[qb & 3][i] : Xl[qb & 3][i];
-        const T xa = (qa & 4) ? Xh[qa & 3][i] : Xl[qa & 3][i];
-        G[i][m] = xb - xa;
-      }
-    }
-    const T ct = c[t], nct = -c[t], c2 = c[t] + c[t], nc2 = -c2;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int qa = tet_corner(t, k), qb = tet_corner(t, k + 1), m = perm(t, k);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        if (i == m) {
-          Y[qb][i] = fma(c2, G[m][m], Y[qb][i]);
-          Y[qa][i] = fma(nc2, G[m][m], Y[qa][i]);
-        } else {
-          const T sv = G[i][m] + G[m][i];
-          Y[qb][i] = fma(ct, sv, Y[qb][i]);
-          Y[qa][i] = fma(nct, sv, Y[qa][i]);
-        }
-      }
-    }
-  }
-}
-
-// Velocity block plus the divergence pieces on the finest grid: with the
-// fine-grid pressure q = P p (component 3 of the tile) the element adds
-// -(h^2/6) qbar_T G_a to the velocity row of vertex a (that is -B_f^T q with
-// B_f the P1-P1 divergence, |T| g = (h^2/6) G) and (h^2/24) tr(Gx) to the
-// scalar row of each vertex ((|T|/4) div u).  c[t] = eta_t h/6, hq = h^2/6.
-template <typename T>
-__device__ __forceinline__ void cube_stokes(const T (&Xl)[4][4], const T (&Xh)[4][4], const T (&c)[6], const T hq,
-                                            T (&Y)[8][4]) {
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    T G[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int qa = tet_corner(t, k), qb = tet_corner(t, k + 1), m = perm(t, k);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T xb = (qb & 4) ? Xh[qb & 3][i] : Xl[qb & 3][i];
-        const T xa = (qa & 4) ? Xh[qa & 3][i] : Xl[qa & 3][i];
-        G[i][m] = xb - xa;
-      }
-    }
-    T qsum = T(0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int q = tet_corner(t, a);
-      qsum += (q & 4) ? Xh[q & 3][3] : Xl[q & 3][3];
-    }
-    const T pq = T(0.25) * hq * qsum;  // (h^2/6) qbar
-    const T ct = c[t], nct = -c[t], c2 = c[t] + c[t];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int qa = tet_corner(t, k), qb = tet_corner(t, k + 1), m = perm(t, k);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        if (i == m) {
-          const T dm = fma(c2, G[m][m], -pq);
-          Y[qb][i] += dm;
-          Y[qa][i] -= dm;
-        } else {
-          const T sv = G[i][m] + G[m][i];
-          Y[qb][i] = fma(ct, sv, Y[qb][i]);
-          Y[qa][i] = fma(nct, sv, Y[qa][i]);
-        }
-      }
-    }
-    const T dv = T(0.25) * hq * (G[0][0] + G[1][1] + G[2][2]);  // (|T|/4) div u
-#pragma unroll
-    for (int a = 0; a < 4; ++a) Y[tet_corner(t, a)][3] += dv;
-  }
-}
 
 // cp.async (LDGSTS) helpers: asynchronous global -> shared copies, zero fill
 // when src_bytes == 0 (the source address is then not read).
@@ -166,16 +80,17 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   T* cfs = reinterpret_cast<T*>(smem_raw + stencil_tile_bytes<TS, BX, BY, MODE>());
   T* cs = cfs + 2 * NT * 6;
 
+  // 32-bit indices: the host limits grids to 3 (n+1)^3 < 2^31 and 6 n^3 < 2^31
   const int n = op.n;
   const int nv = n + 1;
-  const int64_t V = (int64_t)nv * nv * nv;
-  const int64_t plane = (int64_t)nv * nv;
+  const int V = nv * nv * nv;
+  const int plane = nv * nv;
   const int tid = ty * BX + tx;
   const int z0 = bz * zch;
   const int z1 = min(z0 + zch, nv);
   const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
   const bool cube_xy = (cx >= 0) && (cx < n) && (cy >= 0) && (cy < n);
-  const int64_t cube_col = cx + (int64_t)n * cy;
+  const int cube_col = cx + n * cy;
   const int vx = x0 + tx, vy = y0 + ty;
   const bool owner = (tx < BX - 1) && (ty < BY - 1) && (vx < nv) && (vy < nv);
   const bool inner_xy = (vx > 0) && (vx < n) && (vy > 0) && (vy < n);
@@ -198,24 +113,25 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   }
 
   const int zs = z0 - 1;
-  auto issue_tile = [&](int z) {
-    TS* dst = xs + ((z - zs) % 3) * NF * TSZ;
+  // plane z goes to ring slot `slot` (plane zs + i uses slot i mod 3)
+  auto issue_tile = [&](int z, int slot) {
+    TS* dst = xs + slot * NF * TSZ;
     const bool zin = (z > 0) && (z < n);
     const bool zq = (z >= 0) && (z <= n);
-    const int64_t pb = (int64_t)z * plane;
+    const int pb = z * plane;
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
       if (!(s_flags & (1u << (2 * j)))) continue;
       const int idx = tid + j * NT;
       const bool in = zin && (s_flags & (2u << (2 * j)));
-      const int64_t v = in ? pb + s_col[j] : 0;
+      const int v = in ? pb + s_col[j] : 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (MODE == ST_CHEB_PRE) {
-          cp_async(dst + c * TSZ + idx, a.b + c * V + v, sizeof(TS), in);
-          cp_async(dst + (3 + c) * TSZ + idx, a.invD + c * V + v, sizeof(TS), in);
+          cp_async(dst + c * TSZ + idx, a.b + (c * V + v), sizeof(TS), in);
+          cp_async(dst + (3 + c) * TSZ + idx, a.invD + (c * V + v), sizeof(TS), in);
         } else {
-          cp_async(dst + c * TSZ + idx, a.x + c * V + v, sizeof(TS), in);
+          cp_async(dst + c * TSZ + idx, a.x + (c * V + v), sizeof(TS), in);
         }
       }
       if (MODE == ST_STOKES) {  // fine-grid pressure q = P p lives on every vertex
@@ -227,7 +143,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   auto issue_coef = [&](int kc) {
     T* dst = cfs + (((kc - zs) & 1) * NT + tid) * 6;
     const bool ok = cube_xy && kc >= 0 && kc < n;
-    const T* src = op.coef + (ok ? 6 * (cube_col + (int64_t)kc * n * n) : 0);
+    const T* src = op.coef + (ok ? 6 * (cube_col + kc * n * n) : 0);
     if (sizeof(T) == 4) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) cp_async(dst + 2 * i, src + 2 * i, 8, ok);
@@ -238,8 +154,8 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   };
   // CHEB_PRE: the first Chebyshev iterate x1 = s2 D^-1 b of the slots this
   // thread copied, formed once in shared memory (fields 6..8)
-  auto convert_plane = [&](int z) {
-    TS* t = xs + ((z - zs) % 3) * NF * TSZ;
+  auto convert_plane = [&](int slot) {
+    TS* t = xs + slot * NF * TSZ;
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
       if (!(s_flags & (1u << (2 * j)))) continue;
@@ -249,46 +165,48 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     }
   };
   auto tile_val = [&](const TS* t, int c, int li) -> T {
-    if (MODE == ST_CHEB_PRE) return (T)t[(6 + c) * TSZ + li];
+    if (MODE == ST_CHEB_PRE && c < 3) return (T)t[(6 + c) * TSZ + li];
     return (T)t[c * TSZ + li];
   };
 
   // prologue: planes zs, zs+1 and the coefficients of cube layer zs
-  issue_tile(zs);
-  if (zs + 1 <= n) issue_tile(zs + 1);
+  issue_tile(zs, 0);
+  if (zs + 1 <= n) issue_tile(zs + 1, 1);
   issue_coef(zs);
   cp_commit();
 
-  T Xl[4][NC], Xh[4][NC];
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
 
-  for (int k = zs; k < z1; ++k) {
+  // one cube layer k: Xl holds plane k (loaded here when k == zs), Xh
+  // receives plane k+1; rk = ring slot of plane k
+  auto layer = [&](const int k, const int rk, T(&Xl)[4][NC], T(&Xh)[4][NC]) {
+    const int rk1 = rk == 2 ? 0 : rk + 1, rk2 = rk1 == 2 ? 0 : rk1 + 1;
     // prefetch plane k+2 and the coefficients of layer k+1 while layer k computes
     if (k + 1 < z1) {
-      if (k + 2 <= n) issue_tile(k + 2);
+      if (k + 2 <= n) issue_tile(k + 2, rk2);
       issue_coef(k + 1);
     }
     cp_commit();
     // epilogue inputs of plane k, read early so their latency overlaps the compute
     const bool out_k = owner && k >= z0;
     const bool inner = out_k && inner_xy && k > 0 && k < n;
-    const int64_t vo = vcol + (int64_t)k * plane;
+    const int vo = vcol + k * plane;
     TS eb[3], ed[3], ep[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       eb[c] = ed[c] = ep[c] = TS(0);
       if (inner) {
-        if (MODE == ST_RESID || MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) eb[c] = __ldg(a.b + c * V + vo);
-        if (MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) ed[c] = __ldg(a.invD + c * V + vo);
+        if (MODE == ST_RESID || MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) eb[c] = __ldg(a.b + (c * V + vo));
+        if (MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) ed[c] = __ldg(a.invD + (c * V + vo));
         if (MODE == ST_CHEB_STEP) ep[c] = a.xprev[c * V + vo];
       }
     }
     int32_t f[6];
     if constexpr (COARSE) {
       if (cube_xy && k >= 0 && k < n) {
-        const int2* fp = reinterpret_cast<const int2*>(op.fidx + 6 * (cube_col + (int64_t)k * n * n));
+        const int2* fp = reinterpret_cast<const int2*>(op.fidx + 6 * (cube_col + k * n * n));
         int2 f01 = __ldg(fp), f23 = __ldg(fp + 1), f45 = __ldg(fp + 2);
         f[0] = f01.x; f[1] = f01.y; f[2] = f23.x; f[3] = f23.y; f[4] = f45.x; f[5] = f45.y;
       } else {
@@ -298,20 +216,20 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     }
     cp_wait1();
     if (MODE == ST_CHEB_PRE) {
-      if (k == zs) convert_plane(zs);
-      if (k + 1 <= n) convert_plane(k + 1);
+      if (k == zs) convert_plane(rk);
+      if (k + 1 <= n) convert_plane(rk1);
     }
     __syncthreads();
     {
-      const TS* tl = xs + ((k - zs) % 3) * NF * TSZ;
-      const TS* th = xs + ((k + 1 - zs) % 3) * NF * TSZ;
+      const TS* tl = xs + rk * NF * TSZ;
+      const TS* th = xs + rk1 * NF * TSZ;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int li = (ty + (q >> 1)) * TW + tx + (q & 1);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          if (k == zs) Xl[q][c] = (c < 3) ? tile_val(tl, c, li) : (T)tl[c * TSZ + li];
-          Xh[q][c] = (k + 1 <= n) ? ((c < 3) ? tile_val(th, c, li) : (T)th[c * TSZ + li]) : T(0);
+          if (k == zs) Xl[q][c] = tile_val(tl, c, li);
+          Xh[q][c] = (k + 1 <= n) ? tile_val(th, c, li) : T(0);
         }
       }
       if (MODE == ST_CHEB_PRE && inner) {  // own b and D^-1 on plane k, before the ring slot is reused
@@ -343,7 +261,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
           if (f[t] >= 0) {  // stored Galerkin element: s_e A_e x_e precomputed by gca_apply_kernel
-            const T* yv = op.ye + (int64_t)f[t] * 12;
+            const T* yv = op.ye + f[t] * 12;
 #pragma unroll
             for (int r = 0; r < 12; ++r) {
               const int q = tet_corner(t, r & 3);
@@ -382,23 +300,10 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
       if (out_k) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int64_t i = c * V + vo;
-          TS o = TS(0);
-          if (inner) {
-            const TS xo = (TS)Xl[3][c];  // own vertex value on plane k
-            const TS y = (TS)yk[c];
-            if (MODE == ST_APPLY || MODE == ST_STOKES) {
-              o = y;
-            } else if (MODE == ST_RESID) {
-              o = eb[c] - y;
-            } else if (MODE == ST_CHEB_FIRST) {
-              o = xo + a.s0 * ed[c] * (eb[c] - y);
-            } else if (MODE == ST_CHEB_STEP) {
-              o = xo + a.s0 * (xo - ep[c]) + a.s1 * ed[c] * (eb[c] - y);
-            } else {  // ST_CHEB_PRE: x1 = s2 D^-1 b staged in the tile, x0 = 0
-              o = xo + a.s0 * xo + a.s1 * ed[c] * (eb[c] - y);
-            }
-          }
+          const int i = c * V + vo;
+          // own vertex value on plane k (CHEB_PRE: x1 = s2 D^-1 b staged in the tile)
+          const TS o = inner ? stencil_epilogue<MODE, TS>((TS)Xl[3][c], (TS)yk[c], eb[c], ed[c], ep[c], a.s0, a.s1)
+                             : TS(0);
           if (MODE != ST_STOKES && a.out64)
             a.out64[i] = (double)o;
           else
@@ -407,10 +312,29 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
         if (MODE == ST_STOKES) a.out2[vo] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
       }
     }
+  };
+
+  T Xa[4][NC], Xb[4][NC];
+  int rk = 0;
+  if constexpr (sizeof(T) == 4 && MODE != ST_STOKES) {
+    // the z-march unrolled by two so that the plane registers alternate roles
+    // (no copy of the upper plane into the lower one per layer)
+    for (int k = zs; k < z1; k += 2) {
+      layer(k, rk, Xa, Xb);
+      if (k + 1 >= z1) break;
+      const int rk1 = rk == 2 ? 0 : rk + 1;
+      layer(k + 1, rk1, Xb, Xa);
+      rk = rk1 == 2 ? 0 : rk1 + 1;
+    }
+  } else {  // larger per-layer state: one copy of the layer body keeps it in registers
+    for (int k = zs; k < z1; ++k) {
+      layer(k, rk, Xa, Xb);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) Xl[q][c] = Xh[q][c];
+        for (int c = 0; c < NC; ++c) Xa[q][c] = Xb[q][c];
+      rk = rk == 2 ? 0 : rk + 1;
+    }
   }
 }
 
@@ -465,45 +389,6 @@ __global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
   }
 }
 
-
-// Flagged elements of a coarse level: y_e = s_e A_e x_e (Eq. 2.9, stored
-// Galerkin part), one thread per (element, row), written to op.ye for the
-// stencil kernel to scatter.  x follows the stencil's input convention
-// (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).  A separate
-// launch spreads the clustered flagged elements over the whole GPU; inside
-// the stencil they would serialise in the few warps whose cubes hold them.
-template <typename TS, typename T, bool PRE>
-__device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
-  const int64_t f = id / 12;
-  const int r = (int)(id % 12);
-  const int64_t e = op.list[f];
-  const int t = (int)(e % 6);
-  const int64_t cube = e / 6;
-  const int n = op.n, nv = n + 1;
-  const int64_t V = (int64_t)nv * nv * nv;
-  const int ci = (int)(cube % n), cj = (int)((cube / n) % n), ck = (int)(cube / ((int64_t)n * n));
-  const T* M = op.gca + f * 144 + r * 12;
-  T acc = T(0);
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int q = tet_corner(t, b);
-    const int i = ci + (q & 1), j = cj + ((q >> 1) & 1), k = ck + ((q >> 2) & 1);
-    const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
-    const int64_t v = i + (int64_t)nv * (j + (int64_t)nv * k);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T xv = T(0);
-      if (inner) {
-        if (PRE)
-          xv = (T)(a.s2 * __ldg(a.invD + d * V + v) * __ldg(a.b + d * V + v));
-        else
-          xv = (T)__ldg(a.x + d * V + v);
-      }
-      acc = fma(M[d * 4 + b], xv, acc);
-    }
-  }
-  op.ye[f * 12 + r] = op.gscale ? op.gscale[f] * acc : acc;
-}
 
 template <typename TS, typename T, bool PRE>
 __global__ void gca_apply_kernel(const LevelOp<T> op, const StencilArgs<TS> a) {

@@ -69,6 +69,7 @@ def test_host_only_calls(libagca):
     assert L.agca_create(16, 6, 0, None, ctypes.byref(bad)) == 1   # 32 cubes cannot coarsen 5 times to >= 2
     assert L.agca_create(5, 3, 0, None, ctypes.byref(bad)) == 1    # 10 cubes cannot be halved twice
     assert L.agca_create(4, 2, 7, None, ctypes.byref(bad)) == 1    # unknown precision
+    assert L.agca_create(512, 3, 0, None, ctypes.byref(bad)) == 1  # beyond 32-bit kernel indexing
 
 
 def test_default_levels():
