@@ -152,27 +152,25 @@ template <typename TS, typename T>
 cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s,
                            const TileCfg* cfg = nullptr);
 
+// Tiles of a stencil launch: wide tiles (32 x BY threads) over vertex
+// columns 0 .. 31*gxw-1, narrow tiles (8 x 4BY threads) over x0n .. n; grid =
+// (per_z(), gz) blocks of 32*BY threads.
+struct TileGrid {
+  int gxw = 0, gyw = 0, gxn = 0, gyn = 0, x0n = 0, gz = 0, zch = 0;
+  __host__ __device__ int per_z() const { return gxw * gyw + gxn * gyn; }
+};
+TileGrid stencil_tiles(int n, int by, int zch_req);
+
 // ------------------------------------------------------------ batched forms
 // One (problem, level) operator application inside a batched launch.
 template <typename TS, typename T>
 struct StencilTask {
   LevelOp<T> op;
   StencilArgs<TS> a;
-  int zch, gx, gy, gz;
+  TileGrid tg;          // tiles of this problem (8 block rows), tg.per_z() * tg.gz of them
   int64_t tile0;        // first tile of this task in the flattened work list
   const double* sc;     // MINRES scalars of the problem (skip when sc[MS_DONE] != 0) or nullptr
 };
-// tile decomposition used by both the single and the batched launch
-void stencil_grid(int n, int* gx, int* gy, int* gz, int* zch);
-void stencil_grid_by(int n, int by, int zch_req, int* gx, int* gy, int* gz, int* zch);
-// Tiles of a single-operator launch: wide tiles (32 x BY threads) over vertex
-// columns 0 .. 31*gxw-1, narrow tiles (8 x 4BY threads) over x0n .. n; grid =
-// (per_z(), gz) blocks of 32*BY threads.
-struct TileGrid {
-  int gxw = 0, gyw = 0, gxn = 0, gyn = 0, x0n = 0, gz = 0, zch = 0;
-  int per_z() const { return gxw * gyw + gxn * gyn; }
-};
-TileGrid stencil_tiles(int n, int by, int zch_req);
 // tasks: device array, ntiles = total tiles of all tasks; coarse launches
 // first run the stored-Galerkin products of every task (max_gca_rows = the
 // largest n_flag * 12)

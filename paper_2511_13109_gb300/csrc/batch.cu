@@ -25,12 +25,12 @@ __global__ void restrict_batch_kernel(const XferTask* __restrict__ tasks) {
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
   const int nf = tk.nf, nvf = nf + 1, nvc = nf / 2 + 1;
-  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int Vc = nvc * nvc * nvc, Vf = nvf * nvf * nvf;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= Vc) return;
   const T* rf = static_cast<const T*>(tk.src);
   T* rc = static_cast<T*>(tk.dst);
-  const int I = (int)(id % nvc), J = (int)((id / nvc) % nvc), K = (int)(id / ((int64_t)nvc * nvc));
+  const int t = id / nvc, I = id - t * nvc, K = t / nvc, J = t - K * nvc;
   for (int c = 0; c < tk.ncomp; ++c)
     rc[c * Vc + id] = restrict_point<T>(nf, tk.mask, (T)tk.scale, rf + c * Vf, I, J, K);
 }
@@ -41,12 +41,12 @@ __global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
   const XferTask tk = tasks[blockIdx.y];
   if (skip(tk.sc)) return;
   const int nf = tk.nf, nvf = nf + 1, nvc = nf / 2 + 1;
-  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int Vc = nvc * nvc * nvc, Vf = nvf * nvf * nvf;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= Vf) return;
   const T* ec = static_cast<const T*>(tk.src);
   T* xf = static_cast<T*>(tk.dst);
-  const int i = (int)(id % nvf), j = (int)((id / nvf) % nvf), k = (int)(id / ((int64_t)nvf * nvf));
+  const int t = id / nvf, i = id - t * nvf, k = t / nvf, j = t - k * nvf;
   for (int c = 0; c < tk.ncomp; ++c) {
     const T v = prolong_point<T>(nf, tk.mask, ec + c * Vc, i, j, k);
     if (ADD)

@@ -740,6 +740,7 @@ struct BatchStep {
 
 struct agca_batch {
   int n = 0, prec = 0;
+  int sms = 152;             // multiprocessors of the device (read at setup)
   cudaStream_t stream = nullptr;
   std::vector<agca_ctx*> ctx;
   std::vector<size_t> ws_off, gs_off;
@@ -799,8 +800,7 @@ StencilTask<TS, T> make_task(agca_ctx* c, int l, int mode, const TS* x, const TS
   tk.a.s0 = (TS)s0;
   tk.a.s1 = (TS)s1;
   tk.a.s2 = (TS)s2;
-  stencil_grid(c->lev[l].n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
-  tk.sc = sc;
+  tk.sc = sc;  // tiles: push_stencil
   (void)mode;
   return tk;
 }
@@ -809,10 +809,18 @@ template <typename TS, typename T>
 void push_stencil(agca_batch* b, std::vector<BatchStep>& steps, int mode, bool coarse, std::vector<StencilTask<TS, T>> t,
                   int prec) {
   if (t.empty()) return;
+  // one z-chunk for the whole step: about six waves of resident blocks over
+  // all problems (the batch supplies the parallelism, so chunks stay long and
+  // the z-halo small), between 4 and 32 planes
+  int64_t cols = 0;
+  for (const auto& tk : t) cols += (int64_t)stencil_tiles(tk.op.n, 8, 0).per_z() * (tk.op.n + 1);
+  const int64_t slots = 6 * (int64_t)b->sms * 3;
+  const int zch = (int)std::min<int64_t>(32, std::max<int64_t>(4, (cols + slots - 1) / slots));
   int64_t tiles = 0, gca = 0;
   for (auto& tk : t) {
+    tk.tg = stencil_tiles(tk.op.n, 8, zch);
     tk.tile0 = tiles;
-    tiles += (int64_t)tk.gx * tk.gy * tk.gz;
+    tiles += (int64_t)tk.tg.per_z() * tk.tg.gz;
     gca = std::max<int64_t>(gca, tk.op.n_flag * 12);
   }
   BatchStep st{0, mode, prec, coarse, push_tasks(b, t), (int)t.size(), tiles, coarse ? gca : 0, 0};
@@ -985,7 +993,6 @@ void build_stokes(agca_batch* b, std::vector<BatchStep>& steps, const std::vecto
       tk.a.q = c->qfine;
       tk.a.out = y[p];
       tk.a.out2 = c->sfine;
-      stencil_grid(lf.n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
       tk.sc = sc;
       t32.push_back(tk);
     } else {
@@ -995,7 +1002,6 @@ void build_stokes(agca_batch* b, std::vector<BatchStep>& steps, const std::vecto
       tk.a.q = c->qfine;
       tk.a.out = y[p];
       tk.a.out2 = c->sfine;
-      stencil_grid(lf.n, &tk.gx, &tk.gy, &tk.gz, &tk.zch);
       tk.sc = sc;
       t64.push_back(tk);
     }
@@ -1646,6 +1652,9 @@ agca_status agca_batch_setup(agca_batch* b) {
     const agca_status st = agca_setup(b->ctx[i]);
     if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
   }
+  int dev = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
   // task tables of the lockstep MINRES iteration (both buffer parities)
   b->host_tab.clear();
   build_iteration(b, 0);

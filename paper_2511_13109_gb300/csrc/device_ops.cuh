@@ -113,13 +113,12 @@ __device__ __forceinline__ void cube_stokes(const T (&Xl)[4][4], const T (&Xh)[4
 template <typename TS, typename T, bool PRE>
 __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
   const int64_t f = id / 12;
-  const int r = (int)(id % 12);
-  const int64_t e = op.list[f];
-  const int t = (int)(e % 6);
-  const int64_t cube = e / 6;
+  const int r = (int)(id - f * 12);
+  const int e = op.list[f];
+  const int cube = e / 6, t = e - cube * 6;
   const int n = op.n, nv = n + 1;
-  const int64_t V = (int64_t)nv * nv * nv;
-  const int ci = (int)(cube % n), cj = (int)((cube / n) % n), ck = (int)(cube / ((int64_t)n * n));
+  const int V = nv * nv * nv;
+  const int q0 = cube / n, ci = cube - q0 * n, ck = q0 / n, cj = q0 - ck * n;
   const T* M = op.gca + f * 144 + r * 12;
   T acc = T(0);
 #pragma unroll
@@ -127,7 +126,7 @@ __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<
     const int q = tet_corner(t, b);
     const int i = ci + (q & 1), j = cj + ((q >> 1) & 1), k = ck + ((q >> 2) & 1);
     const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
-    const int64_t v = i + (int64_t)nv * (j + (int64_t)nv * k);
+    const int v = i + nv * (j + nv * k);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       T xv = T(0);
@@ -179,11 +178,11 @@ __device__ __forceinline__ T restrict_point(const int nf, const bool mask, const
   for (int d = 1; d < 8; ++d) {
     const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
     if (fi + dx <= nf && fj + dy <= nf && fk + dz <= nf)
-      acc += __ldg(r + (fi + dx) + (int64_t)nvf * ((fj + dy) + (int64_t)nvf * (fk + dz)));
+      acc += __ldg(r + (fi + dx) + nvf * ((fj + dy) + nvf * (fk + dz)));
     if (fi - dx >= 0 && fj - dy >= 0 && fk - dz >= 0)
-      acc += __ldg(r + (fi - dx) + (int64_t)nvf * ((fj - dy) + (int64_t)nvf * (fk - dz)));
+      acc += __ldg(r + (fi - dx) + nvf * ((fj - dy) + nvf * (fk - dz)));
   }
-  return scale * (__ldg(r + fi + (int64_t)nvf * (fj + (int64_t)nvf * fk)) + T(0.5) * acc);
+  return scale * (__ldg(r + fi + nvf * (fj + nvf * fk)) + T(0.5) * acc);
 }
 
 // (P e)(i, j, k) for one component e of the coarse grid of a fine grid with
@@ -194,9 +193,9 @@ __device__ __forceinline__ T prolong_point(const int nf, const bool mask, const 
   if (mask && (i == 0 || j == 0 || k == 0 || i == nf || j == nf || k == nf)) return T(0);
   const int nvc = nf / 2 + 1;
   const int I = i >> 1, J = j >> 1, K = k >> 1, dx = i & 1, dy = j & 1, dz = k & 1;
-  const T e0 = __ldg(e + I + (int64_t)nvc * (J + (int64_t)nvc * K));
+  const T e0 = __ldg(e + I + nvc * (J + nvc * K));
   if (!(dx | dy | dz)) return e0;
-  return T(0.5) * (e0 + __ldg(e + (I + dx) + (int64_t)nvc * ((J + dy) + (int64_t)nvc * (K + dz))));
+  return T(0.5) * (e0 + __ldg(e + (I + dx) + nvc * ((J + dy) + nvc * (K + dz))));
 }
 
 // ------------------------------------------------------------- coarsest solve
@@ -236,10 +235,9 @@ __device__ __forceinline__ void coarse_solve_block(const int n, const double* __
     if (lane == 0) rs[q] = s;
   }
   __syncthreads();
-  for (int64_t id = threadIdx.x; id < 3 * V; id += blockDim.x) {
-    const int c = (int)(id / V);
-    const int64_t v = id % V;
-    const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  for (int id = threadIdx.x; id < 3 * (int)V; id += blockDim.x) {
+    const int c = id / (int)V, v = id - c * (int)V;
+    const int t = v / nv, i = v - t * nv, k = t / nv, j = t - k * nv;
     const bool inner = i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
     T out = T(0);
     if (inner) out = (T)rs[c * nI + (i - 1) + ni * ((j - 1) + ni * (k - 1))];

@@ -249,10 +249,24 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
       for (int c = 0; c < NC; ++c) Y[q][c] = T(0);
 
     if (cube_xy && k >= 0 && k < n) {
+      // this cube's 6 coefficients: three 8-byte (FP32) or 16-byte (FP64) shared loads
       const T* cp = cfs + (((k - zs) & 1) * NT + tid) * 6;
       T cf[6];
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-      for (int t = 0; t < 6; ++t) cf[t] = cp[t] * op.h6;
+        for (int i = 0; i < 3; ++i) {
+          const float2 v = reinterpret_cast<const float2*>(cp)[i];
+          cf[2 * i] = v.x * op.h6;
+          cf[2 * i + 1] = v.y * op.h6;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const double2 v = reinterpret_cast<const double2*>(cp)[i];
+          cf[2 * i] = v.x * op.h6;
+          cf[2 * i + 1] = v.y * op.h6;
+        }
+      }
       if constexpr (COARSE) {
 #pragma unroll
         for (int t = 0; t < 6; ++t)
@@ -370,21 +384,37 @@ __global__ void __launch_bounds__(32 * BY, stencil_min_blocks<T, BY>())
 
 // Persistent batched form: one launch applies the same stencil mode to many
 // independent problems; every CTA walks the flattened (problem, tile) work
-// list, skipping problems whose MINRES has converged.
-template <typename TS, typename T, int BX, int BY, int MODE, bool COARSE>
-__global__ void __launch_bounds__(BX* BY, stencil_min_blocks<T, BY>())
+// list (both tile classes, as stencil_kernel), skipping problems whose MINRES
+// has converged.
+template <typename TS, typename T, int BY, int MODE, bool COARSE>
+__global__ void __launch_bounds__(32 * BY, stencil_min_blocks<T, BY>())
     stencil_batch_kernel(const StencilTask<TS, T>* __restrict__ tasks, const int ntasks, const int64_t ntiles) {
   grid_dep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
   for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    int j = 0;
-    while (j + 1 < ntasks && tasks[j + 1].tile0 <= it) ++j;
-    const StencilTask<TS, T> tk = tasks[j];
+    int lo = 0, hi = ntasks - 1;  // last task with tile0 <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= it)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const StencilTask<TS, T>& tk = tasks[lo];
     if (tk.sc && tk.sc[MS_DONE] != 0.0) continue;  // converged problem
-    const int64_t local = it - tk.tile0;
-    const int bx = (int)(local % tk.gx), by = (int)((local / tk.gx) % tk.gy), bz = (int)(local / ((int64_t)tk.gx * tk.gy));
-    stencil_block<TS, T, BX, BY, MODE, COARSE>(tk.op, tk.a, tk.zch, bx * (BX - 1), by * (BY - 1), bz, threadIdx.x,
-                                               threadIdx.y, smem_raw);
+    const TileGrid tg = tk.tg;
+    const int local = (int)(it - tk.tile0), per = tg.per_z();
+    const int bz = local / per, t = local % per, nw = tg.gxw * tg.gyw;
+    if (t < nw) {
+      stencil_block<TS, T, 32, BY, MODE, COARSE>(tk.op, tk.a, tg.zch, (t % tg.gxw) * 31, (t / tg.gxw) * (BY - 1), bz,
+                                                 tid & 31, tid >> 5, smem_raw);
+    } else {
+      constexpr int BYN = 4 * BY;
+      const int u = t - nw;
+      stencil_block<TS, T, 8, BYN, MODE, COARSE>(tk.op, tk.a, tg.zch, tg.x0n + (u % tg.gxn) * 7,
+                                                 (u / tg.gxn) * (BYN - 1), bz, tid & 7, tid >> 3, smem_raw);
+    }
     __syncthreads();  // the shared-memory rings are reused by the next tile
   }
 }
@@ -455,7 +485,7 @@ cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a
   return cudaGetLastError();
 }
 
-template <typename TS, typename T, int BX, int BY, bool COARSE>
+template <typename TS, typename T, int BY, bool COARSE>
 cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                               int64_t max_gca_rows, cudaStream_t s) {
   if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
@@ -471,20 +501,20 @@ cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int nta
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int per_sm = sizeof(T) == 4 ? 3 : 2;
-  const int64_t nb = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  dim3 grid((unsigned)nb), block(BX, BY);
+  const int64_t nb = std::min<int64_t>(ntiles, (int64_t)sms * stencil_min_blocks<T, BY>());
+  const dim3 grid((unsigned)nb), block(32 * BY);
 #define AGCA_BLAUNCH(M, C)                                                                                 \
   do {                                                                                                     \
-    constexpr size_t smem = stencil_smem_bytes<TS, T, BX, BY, M>();                                       \
+    constexpr size_t smem = std::max(stencil_smem_bytes<TS, T, 32, BY, M>(),                              \
+                                     stencil_smem_bytes<TS, T, 8, 4 * BY, M>());                          \
     static bool attr_set[64] = {};                                                                        \
     if (smem > 48 * 1024 && dev >= 0 && dev < 64 && !attr_set[dev]) {                                    \
-      e = cudaFuncSetAttribute(stencil_batch_kernel<TS, T, BX, BY, M, C>,                                 \
+      e = cudaFuncSetAttribute(stencil_batch_kernel<TS, T, BY, M, C>,                                     \
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
       if (e != cudaSuccess) return e;                                                                     \
       attr_set[dev] = true;                                                                               \
     }                                                                                                     \
-    KL(launch_k(stencil_batch_kernel<TS, T, BX, BY, M, C>, grid, block, smem, s, tasks, ntasks, ntiles)); \
+    KL(launch_k(stencil_batch_kernel<TS, T, BY, M, C>, grid, block, smem, s, tasks, ntasks, ntiles));     \
   } while (0)
   switch (mode) {
     case ST_RESID: AGCA_BLAUNCH(ST_RESID, COARSE); break;
@@ -505,28 +535,6 @@ cudaError_t launch_batch_mode(int mode, const StencilTask<TS, T>* tasks, int nta
 }
 
 }  // namespace
-
-void stencil_grid(int n, int* gx_out, int* gy_out, int* gz_out, int* zch_out) {
-  stencil_grid_by(n, 8, 0, gx_out, gy_out, gz_out, zch_out);
-}
-
-void stencil_grid_by(int n, int BY, int zch_req, int* gx_out, int* gy_out, int* gz_out, int* zch_out) {
-  constexpr int BX = 32;
-  const int nv = n + 1;
-  const int gx = (nv + BX - 2) / (BX - 1), gy = (nv + BY - 2) / (BY - 1);
-  // default: enough blocks for two waves of 3 resident 256-thread blocks per
-  // SM; small grids get short z-chunks (latency bound), large ones long
-  // chunks (less z-halo).  zch_req > 0 (autotuner) overrides.
-  int gz = (912 * 8 / BY + gx * gy - 1) / (gx * gy);
-  int zch = zch_req > 0 ? zch_req : (nv + gz - 1) / gz;
-  if (zch < 1) zch = 1;
-  if (zch > nv) zch = nv;
-  gz = (nv + zch - 1) / zch;
-  *gx_out = gx;
-  *gy_out = gy;
-  *gz_out = gz;
-  *zch_out = zch;
-}
 
 TileGrid stencil_tiles(int n, int BY, int zch_req) {
   const int nv = n + 1;
@@ -549,7 +557,8 @@ TileGrid stencil_tiles(int n, int BY, int zch_req) {
   if (g.gxn == 0) g.gyn = 0;
   const int per = g.per_z();
   // default: enough blocks for two waves of 3 resident 256-thread blocks per
-  // SM (as stencil_grid_by); zch_req > 0 (autotuner) overrides
+  // SM; small grids get short z-chunks (latency bound), large ones long
+  // chunks (less z-halo).  zch_req > 0 (autotuner, batches) overrides
   int gz = (912 * 8 / BY + per - 1) / per;
   int zch = zch_req > 0 ? zch_req : (nv + gz - 1) / gz;
   if (zch < 1) zch = 1;
@@ -562,8 +571,8 @@ TileGrid stencil_tiles(int n, int BY, int zch_req) {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s) {
-  if (coarse) return launch_batch_mode<TS, T, 32, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
-  return launch_batch_mode<TS, T, 32, 8, false>(mode, tasks, ntasks, ntiles, 0, s);
+  if (coarse) return launch_batch_mode<TS, T, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
+  return launch_batch_mode<TS, T, 8, false>(mode, tasks, ntasks, ntiles, 0, s);
 }
 template cudaError_t launch_stencil_batch<float, float>(int, bool, const StencilTask<float, float>*, int, int64_t,
                                                         int64_t, cudaStream_t);

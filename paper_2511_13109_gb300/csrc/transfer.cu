@@ -13,12 +13,11 @@ namespace {
 template <typename T>
 __global__ void restrict_kernel(int nf, int ncomp, bool mask, T scale, const T* __restrict__ rf, T* __restrict__ rc) {
   grid_dep_entry();
-  const int nc = nf / 2;
-  const int nvf = nf + 1, nvc = nc + 1;
-  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nvf = nf + 1, nvc = nf / 2 + 1;
+  const int Vc = nvc * nvc * nvc, Vf = nvf * nvf * nvf;  // 32-bit: grids are limited on the host
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= Vc) return;
-  const int I = (int)(id % nvc), J = (int)((id / nvc) % nvc), K = (int)(id / ((int64_t)nvc * nvc));
+  const int t = id / nvc, I = id - t * nvc, K = t / nvc, J = t - K * nvc;
   for (int c = 0; c < ncomp; ++c) rc[c * Vc + id] = restrict_point<T>(nf, mask, scale, rf + c * Vf, I, J, K);
 }
 
@@ -26,10 +25,10 @@ template <typename T, bool ADD>
 __global__ void prolong_kernel(int nf, int ncomp, bool mask, const T* __restrict__ ec, T* __restrict__ xf) {
   grid_dep_entry();
   const int nvf = nf + 1, nvc = nf / 2 + 1;
-  const int64_t Vc = (int64_t)nvc * nvc * nvc, Vf = (int64_t)nvf * nvf * nvf;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int Vc = nvc * nvc * nvc, Vf = nvf * nvf * nvf;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= Vf) return;
-  const int i = (int)(id % nvf), j = (int)((id / nvf) % nvf), k = (int)(id / ((int64_t)nvf * nvf));
+  const int t = id / nvf, i = id - t * nvf, k = t / nvf, j = t - k * nvf;
   for (int c = 0; c < ncomp; ++c) {
     const T v = prolong_point<T>(nf, mask, ec + c * Vc, i, j, k);
     if (ADD)
