@@ -50,7 +50,7 @@ __global__ void prolong_batch_kernel(const XferTask* __restrict__ tasks) {
   for (int c = 0; c < tk.ncomp; ++c) {
     const T v = prolong_point<T>(nf, tk.mask, ec + c * Vc, i, j, k);
     if (ADD)
-      xf[c * Vf + id] += v;
+      xf[c * Vf + id] = add_rn(xf[c * Vf + id], v);
     else
       xf[c * Vf + id] = v;
   }

@@ -100,6 +100,11 @@ struct agca_ctx {
     int64_t launches;
   };
   std::vector<GraphEntry> graphs;
+  // two MINRES iterations (the buffer rotation returns after two) replayed
+  // from a CUDA graph; [0]: FP64 operator, [1]: FP32-compute operator
+  cudaGraphExec_t minres_graph[2] = {nullptr, nullptr};
+  const double* minres_key[2] = {nullptr, nullptr};  // the correction vector d the graph updates
+  int64_t minres_launches[2] = {0, 0};
   bool use_graphs = true;
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -114,6 +119,11 @@ struct agca_ctx {
   void clear_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     graphs.clear();
+    for (int i = 0; i < 2; ++i) {
+      if (minres_graph[i]) cudaGraphExecDestroy(minres_graph[i]);
+      minres_graph[i] = nullptr;
+      minres_key[i] = nullptr;
+    }
   }
 
   agca_status fail(agca_status s, const std::string& msg) {
@@ -529,9 +539,8 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
   CKS(precond_impl(ctx, v, z));
   CKS(dot1(ctx, z, v, nt, ctx->sc + MS_DOT_ZV));
   LK(1, launch_minres_init(ctx->sc, tol_rel, s));
-  const int check_every = ctx->check_every;
-  int it = 0;
-  for (; it < maxit; ++it) {
+  // one iteration; after it the buffer roles rotate (v, z, w pairs swap)
+  auto iteration = [&]() -> agca_status {
     CKS(stokes_dispatch(ctx, z, kz, low));
     CKS(dot1(ctx, kz, z, nt, ctx->sc + MS_DOT_KZZ));
     LK(1, launch_lanczos(nt, kz, v, vold, ctx->sc, s));  // vold <- v_new
@@ -542,7 +551,50 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
     std::swap(vold, v);
     std::swap(z, zn);
     std::swap(wold, w);
-    if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+    return AGCA_OK;
+  };
+  // iterations past convergence change nothing (the device scalars freeze the
+  // update), so the loop may run a few beyond it between host checks
+  const int gi = low ? 1 : 0;
+  bool graph = ctx->use_graphs && !ctx->prof && s != nullptr;
+  if (graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    graph = (cs == cudaStreamCaptureStatusNone);
+  }
+  if (graph && (ctx->minres_graph[gi] == nullptr || ctx->minres_key[gi] != d)) {
+    if (ctx->minres_graph[gi]) cudaGraphExecDestroy(ctx->minres_graph[gi]);
+    ctx->minres_graph[gi] = nullptr;
+    const int64_t l0 = ctx->launches;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    agca_status st = iteration();
+    if (st == AGCA_OK) st = iteration();
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    ctx->minres_launches[gi] = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != AGCA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (ee != cudaSuccess) return ctx->fail(AGCA_ECUDA, std::string("MINRES capture: ") + cudaGetErrorString(ee));
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->minres_graph[gi], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return ctx->fail(AGCA_ECUDA, std::string("MINRES graph: ") + cudaGetErrorString(ie));
+    ctx->minres_key[gi] = d;
+  }
+  const int check_every = ctx->check_every;
+  int it = 0;
+  while (it < maxit) {
+    if (graph && maxit - it >= 2) {  // two iterations per replay: the buffer roles return
+      CK(cudaGraphLaunch(ctx->minres_graph[gi], s));
+      ctx->launches += ctx->minres_launches[gi];
+      it += 2;
+    } else {
+      CKS(iteration());
+      it += 1;
+    }
+    if (it % check_every < (graph ? 2 : 1) || it >= maxit) {
       double done = 0.0;
       CKS(read_scalar(ctx, ctx->sc + MS_DONE, &done));
       if (done != 0.0) break;
@@ -653,7 +705,24 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   const bool f32 = sizeof(T) == 4;
   std::vector<int> bys = f32 ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
   const int nv = lv.n + 1;
-  std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  int dev = 0, sms = 152;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // z-chunk candidates: a fixed ladder plus, per block-row count, the chunks
+  // whose block count fills k = 1..8 whole waves of resident blocks (no
+  // partly filled last wave)
+  auto candidates = [&](int by) {
+    std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    const int per_sm = f32 ? (by <= 8 ? 3 : (by <= 12 ? 2 : 1)) : 2;
+    const int per_z = stencil_tiles(lv.n, by, 1).per_z();
+    for (int k = 1; k <= 8; ++k) {
+      const int gz = std::max(1, k * sms * per_sm / per_z);
+      zs.push_back((nv + gz - 1) / gz);
+    }
+    std::sort(zs.begin() + 1, zs.end());
+    zs.erase(std::unique(zs.begin() + 1, zs.end()), zs.end());
+    return zs;
+  };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -671,7 +740,7 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
     float best_ms = 1e30f;
     for (int by : bys) {
       int last_zch = -1;
-      for (int zr : zs) {
+      for (int zr : candidates(by)) {
         if (zr > nv) continue;
         const int zch = stencil_tiles(lv.n, by, zr).zch;
         if (zch == last_zch) continue;
@@ -748,6 +817,8 @@ struct agca_batch {
   char* ws = nullptr;
   char* gs = nullptr;
   char* tab = nullptr;       // device task tables
+  std::vector<int> members;       // problems the table builders cover
+  std::vector<int> iter_members;  // problems the captured iteration graph covers
   double* partials = nullptr;
   std::vector<char> host_tab;
   std::vector<BatchStep> iter_steps[2];  // MINRES iteration, by buffer parity
@@ -855,7 +926,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   const int pr = std::is_same<T, float>::value ? 1 : 0;
   const bool mixed = std::is_same<T, float>::value;
   int maxL = 0;
-  for (auto* c : b->ctx) maxL = std::max(maxL, c->L);
+  for (int p : b->members) maxL = std::max(maxL, b->ctx[p]->L);
   auto sc_of = [&](int p) -> const double* { return skip_done ? b->ctx[p]->sc : nullptr; };
   auto bfine = [&](int p) -> const T* {
     agca_ctx* c = b->ctx[p];
@@ -863,7 +934,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   };
   if (mixed) {
     std::vector<XferTask> t;
-    for (int p = 0; p < P; ++p) {
+    for (int p : b->members) {
       agca_ctx* c = b->ctx[p];
       XferTask x{};
       x.count = 3 * c->lev[c->L].V;
@@ -878,7 +949,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   for (int d = 0; d <= maxL - 2; ++d) {
     std::vector<StencilTask<T, T>> pre, res;
     std::vector<XferTask> rst;
-    for (int p = 0; p < P; ++p) {
+    for (int p : b->members) {
       agca_ctx* c = b->ctx[p];
       const int l = c->L - d;
       if (l < 2) continue;
@@ -907,7 +978,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   }
   {
     std::vector<XferTask> t;
-    for (int p = 0; p < P; ++p) {
+    for (int p : b->members) {
       agca_ctx* c = b->ctx[p];
       XferTask x{};
       x.nf = c->lev[1].n;
@@ -924,7 +995,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   for (int d = maxL - 2; d >= 0; --d) {
     std::vector<StencilTask<T, T>> first, step;
     std::vector<XferTask> pro;
-    for (int p = 0; p < P; ++p) {
+    for (int p : b->members) {
       agca_ctx* c = b->ctx[p];
       const int l = c->L - d;
       if (l < 2) continue;
@@ -952,7 +1023,7 @@ void build_cycle(agca_batch* b, std::vector<BatchStep>& steps, const std::vector
   }
   {
     std::vector<XferTask> t;
-    for (int p = 0; p < P; ++p) {
+    for (int p : b->members) {
       agca_ctx* c = b->ctx[p];
       XferTask x{};
       x.count = 3 * c->lev[c->L].V;
@@ -972,7 +1043,7 @@ void build_stokes(agca_batch* b, std::vector<BatchStep>& steps, const std::vecto
   std::vector<XferTask> pro, rst;
   std::vector<StencilTask<double, double>> t64;
   std::vector<StencilTask<double, float>> t32;
-  for (int p = 0; p < P; ++p) {
+  for (int p : b->members) {
     agca_ctx* c = b->ctx[p];
     const Level& lf = c->lev[c->L];
     const int64_t n3 = 3 * lf.V;
@@ -1032,7 +1103,7 @@ void build_iteration(agca_batch* b, int par) {
   const bool mixed = b->prec == AGCA_MIXED;
   std::vector<const double*> z(P), vnew_c(P);
   std::vector<double*> kz(P), vnew(P), zn(P);
-  for (int p = 0; p < P; ++p) {
+  for (int p : b->members) {
     agca_ctx* c = b->ctx[p];
     z[p] = c->kv[par ? KV_ZNEW : KV_Z];
     zn[p] = c->kv[par ? KV_Z : KV_ZNEW];
@@ -1042,7 +1113,7 @@ void build_iteration(agca_batch* b, int par) {
   }
   build_stokes(b, steps, z, kz, mixed, true);
   std::vector<KTask> dk, lz, pz, ps, pd, pm, dz, up, sc;
-  for (int p = 0; p < P; ++p) {
+  for (int p : b->members) {
     agca_ctx* c = b->ctx[p];
     const int64_t nt = c->nt, n3 = nt - c->Vp;
     const double* v = c->kv[par ? KV_VOLD : KV_V];
@@ -1645,28 +1716,21 @@ agca_status agca_batch_bind_gca_store(agca_batch* b, void* dev_ptr, size_t bytes
   return AGCA_OK;
 }
 
-agca_status agca_batch_setup(agca_batch* b) {
-  if (!b) return AGCA_EINVAL;
-  if (!b->ws || !b->gs) return b->fail(AGCA_ESTATE, "bind the workspace and the Galerkin store first");
-  for (int i = 0; i < b->n; ++i) {
-    const agca_status st = agca_setup(b->ctx[i]);
-    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
-  }
-  int dev = 0;
-  BCK(cudaGetDevice(&dev));
-  BCK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
-  // task tables of the lockstep MINRES iteration (both buffer parities)
+// Task tables and captured graph of the lockstep MINRES iteration (both
+// buffer parities) for the problems in b->members.
+agca_status build_iteration_graph(agca_batch* b) {
+  b->iter_members.clear();
   b->host_tab.clear();
   build_iteration(b, 0);
   build_iteration(b, 1);
-  // publish every problem's done flag into one contiguous array as well
+  // publish every member's done flag into one contiguous array (by problem) as well
   double* done = b->partials + (size_t)b->n * 64;
   for (int par = 0; par < 2; ++par)
     for (BatchStep& st : b->iter_steps[par])
       if (st.kind == 2 && st.mode == KB_SCALARS)
-        for (int p = 0; p < st.ntasks; ++p) {
-          KTask* t = reinterpret_cast<KTask*>(b->host_tab.data() + st.off) + p;
-          t->c = done + p;
+        for (int i = 0; i < st.ntasks; ++i) {
+          KTask* t = reinterpret_cast<KTask*>(b->host_tab.data() + st.off) + i;
+          t->c = done + b->members[i];
         }
   if (b->host_tab.size() > b->tab_bytes / 3 * 2) return b->fail(AGCA_EINTERNAL, "batch task table overflow");
   BCK(cudaMemcpyAsync(b->tab, b->host_tab.data(), b->host_tab.size(), cudaMemcpyHostToDevice, b->stream));
@@ -1693,6 +1757,23 @@ agca_status agca_batch_setup(agca_batch* b) {
     BCK(ie);
     b->iter_launches = nl;
   }
+  b->iter_members = b->members;
+  return AGCA_OK;
+}
+
+agca_status agca_batch_setup(agca_batch* b) {
+  if (!b) return AGCA_EINVAL;
+  if (!b->ws || !b->gs) return b->fail(AGCA_ESTATE, "bind the workspace and the Galerkin store first");
+  for (int i = 0; i < b->n; ++i) {
+    const agca_status st = agca_setup(b->ctx[i]);
+    if (st != AGCA_OK) return b->fail(st, b->ctx[i]->err);
+  }
+  int dev = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+  b->members.resize(b->n);
+  for (int i = 0; i < b->n; ++i) b->members[i] = i;
+  BCKS(build_iteration_graph(b));
   b->setup_done = true;
   return AGCA_OK;
 }
@@ -1708,6 +1789,8 @@ agca_status agca_batch_vcycle(agca_batch* b, const double* const* r_devs, double
   if (!b->setup_done) return b->fail(AGCA_ESTATE, "setup first");
   std::vector<const double*> r(r_devs, r_devs + b->n);
   std::vector<double*> z(z_devs, z_devs + b->n);
+  b->members.resize(b->n);  // a batched V-cycle covers every problem
+  for (int p = 0; p < b->n; ++p) b->members[p] = p;
   std::vector<BatchStep> steps;
   const size_t base = b->host_tab.size();
   if (b->prec == AGCA_MIXED)
@@ -1770,6 +1853,14 @@ agca_status agca_batch_solve(agca_batch* b, const double* const* b_devs, double*
       any = any || active[p];
     }
     if (!any) break;
+    // the lockstep tables cover the problems still above the tolerance
+    std::vector<int> act;
+    for (int p = 0; p < P; ++p)
+      if (active[p]) act.push_back(p);
+    if (act != b->iter_members) {
+      b->members = act;
+      BCKS(build_iteration_graph(b));
+    }
     int budget = 0;
     for (int p = 0; p < P; ++p) {
       agca_ctx* ctx = b->ctx[p];
@@ -1806,10 +1897,16 @@ agca_status agca_batch_solve(agca_batch* b, const double* const* b_devs, double*
       if ((it / 2 + 1) % 4 == 0 || it + 2 >= budget) {
         BCK(cudaMemcpyAsync(done.data(), done_dev, P * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
         BCK(cudaStreamSynchronize(b->stream));
-        bool all = true;
-        for (int p = 0; p < P; ++p)
-          if (active[p] && done[p] == 0.0) all = false;
-        if (all) break;
+        std::vector<int> running;
+        for (int p : b->iter_members)
+          if (done[p] == 0.0) running.push_back(p);
+        if (running.empty()) break;
+        // once a quarter of the lockstep problems have converged, drop them
+        // from the tables: their launches no longer walk converged work
+        if (4 * running.size() <= 3 * b->iter_members.size()) {
+          b->members = running;
+          BCKS(build_iteration_graph(b));
+        }
       }
     }
     for (int p = 0; p < P; ++p) {

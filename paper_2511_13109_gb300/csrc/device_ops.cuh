@@ -8,6 +8,11 @@
 
 namespace agca {
 
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // ------------------------------------------------------------ element action
 // For a tetrahedron with nodal values x_a (a = 0..3) the scaled displacement
 // gradient is Gx = sum_a x_a (x) G_a; along the Kuhn path its column p_k is the
@@ -110,14 +115,14 @@ __device__ __forceinline__ void cube_stokes(const T (&Xl)[4][4], const T (&Xh)[4
 // (boundary entries are zero; CHEB_PRE stages x = s2 D^-1 b).  A separate
 // launch spreads the clustered flagged elements over the whole GPU; inside
 // the stencil they would serialise in the few warps whose cubes hold them.
-template <typename TS, typename T, bool PRE>
-__device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
+// xval(d, v): the operator input (component d, vertex v) on an interior vertex
+template <typename T, typename XF>
+__device__ __forceinline__ void gca_row_of(const LevelOp<T>& op, const int64_t id, XF xval) {
   const int64_t f = id / 12;
   const int r = (int)(id - f * 12);
   const int e = op.list[f];
   const int cube = e / 6, t = e - cube * 6;
   const int n = op.n, nv = n + 1;
-  const int V = nv * nv * nv;
   const int q0 = cube / n, ci = cube - q0 * n, ck = q0 / n, cj = q0 - ck * n;
   const T* M = op.gca + f * 144 + r * 12;
   T acc = T(0);
@@ -129,17 +134,20 @@ __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<
     const int v = i + nv * (j + nv * k);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      T xv = T(0);
-      if (inner) {
-        if (PRE)
-          xv = (T)(a.s2 * __ldg(a.invD + d * V + v) * __ldg(a.b + d * V + v));
-        else
-          xv = (T)__ldg(a.x + d * V + v);
-      }
+      const T xv = inner ? (T)xval(d, v) : T(0);
       acc = fma(M[d * 4 + b], xv, acc);
     }
   }
   op.ye[f * 12 + r] = op.gscale ? op.gscale[f] * acc : acc;
+}
+
+template <typename TS, typename T, bool PRE>
+__device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<TS>& a, const int64_t id) {
+  const int V = (op.n + 1) * (op.n + 1) * (op.n + 1);
+  gca_row_of<T>(op, id, [&](int d, int v) -> TS {
+    if (PRE) return a.s2 * __ldg(a.invD + d * V + v) * __ldg(a.b + d * V + v);
+    return __ldg(a.x + d * V + v);
+  });
 }
 
 // Result of a fused stencil mode at one vertex from the operator value y =
@@ -195,7 +203,8 @@ __device__ __forceinline__ T prolong_point(const int nf, const bool mask, const 
   const int I = i >> 1, J = j >> 1, K = k >> 1, dx = i & 1, dy = j & 1, dz = k & 1;
   const T e0 = __ldg(e + I + nvc * (J + nvc * K));
   if (!(dx | dy | dz)) return e0;
-  return T(0.5) * (e0 + __ldg(e + (I + dx) + nvc * ((J + dy) + nvc * (K + dz))));
+  // explicit roundings: x + (P e) then rounds the same in every kernel that adds it
+  return mul_rn(T(0.5), add_rn(e0, __ldg(e + (I + dx) + nvc * ((J + dy) + nvc * (K + dz)))));
 }
 
 // ------------------------------------------------------------- coarsest solve

@@ -32,7 +32,7 @@ __global__ void prolong_kernel(int nf, int ncomp, bool mask, const T* __restrict
   for (int c = 0; c < ncomp; ++c) {
     const T v = prolong_point<T>(nf, mask, ec + c * Vc, i, j, k);
     if (ADD)
-      xf[c * Vf + id] += v;
+      xf[c * Vf + id] = add_rn(xf[c * Vf + id], v);
     else
       xf[c * Vf + id] = v;
   }

@@ -242,3 +242,26 @@ def test_vcycle_graph_replay_matches_direct(case):
             s.synchronize()
             for o in outs:
                 assert torch.equal(o, ref)
+
+
+@pytest.mark.parametrize("prec", [pkg.FP64, pkg.MIXED])
+def test_solve_graph_replay_matches_direct(case, prec):
+    """On a non-default stream two MINRES iterations are captured into one
+    CUDA graph and replayed; the solution and the iteration count equal those
+    of the direct launches on the default stream."""
+    if case.N > 8:
+        pytest.skip("the small cases cover the capture; 16^3 FP64 solves take a minute each")
+    c0 = pkg.Context(case.N, case.L, prec, device=DEV)
+    c0.prepare(_d(case.eta), case.nu)
+    b = c0.load_vector(_d(case.fbar.ravel()))
+    x0, its0, rel0 = c0.solve(b, 1e-10, 20000)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream(device=DEV)
+    with torch.cuda.stream(s):
+        c1 = pkg.Context(case.N, case.L, prec, device=DEV, stream=s)
+        c1.prepare(_d(case.eta), case.nu)
+        for _ in range(2):  # capture, then replay from the cached graph
+            x1, its1, rel1 = c1.solve(b, 1e-10, 20000)
+            s.synchronize()
+            assert its1 == its0 and rel1 == rel0
+            assert torch.equal(x1, x0)
