@@ -54,11 +54,21 @@ template <typename TS, int BX, int BY, int MODE>
 __host__ __device__ constexpr size_t stencil_tile_bytes() {
   return ((size_t)3 * stencil_tile_fields<MODE, TS>() * (BX + 1) * (BY + 1) * sizeof(TS) + 127) / 128 * 128;
 }
+// Stokes operator with FP64 vectors and FP32 arithmetic: every staged value
+// is converted once, by the thread that copied it, into an FP32 copy of the
+// ring (FP64 -> FP32 conversions issue at the FP64 rate on this GPU, so
+// converting at each of the up to 4 corner reads of a value costs more than
+// the element arithmetic)
+template <typename TS, typename T, int MODE>
+__host__ __device__ constexpr bool stencil_converts() {
+  return MODE == ST_STOKES && sizeof(TS) != sizeof(T);
+}
 template <typename TS, typename T, int BX, int BY, int MODE>
 __host__ __device__ constexpr size_t stencil_smem_bytes() {
   constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;
   return stencil_tile_bytes<TS, BX, BY, MODE>() + (size_t)2 * BX * BY * 6 * sizeof(T) +
-         (size_t)2 * NC * BX * BY * sizeof(T);
+         (size_t)2 * NC * BX * BY * sizeof(T) +
+         (stencil_converts<TS, T, MODE>() ? (size_t)3 * NC * (BX + 1) * (BY + 1) * sizeof(T) : 0);
 }
 
 // One CTA tile of the stencil: vertex columns x0.. and rows y0.. (origin of
@@ -79,6 +89,8 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   TS* xs = reinterpret_cast<TS*>(smem_raw);
   T* cfs = reinterpret_cast<T*>(smem_raw + stencil_tile_bytes<TS, BX, BY, MODE>());
   T* cs = cfs + 2 * NT * 6;
+  constexpr bool CONV = stencil_converts<TS, T, MODE>();
+  T* xcv = cs + 2 * NC * NT;  // CONV: FP32 ring [3][NC][TSZ]
 
   // 32-bit indices: the host limits grids to 3 (n+1)^3 < 2^31 and 6 n^3 < 2^31
   const int n = op.n;
@@ -164,6 +176,18 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
       for (int c = 0; c < 3; ++c) t[(6 + c) * TSZ + idx] = a.s2 * t[(3 + c) * TSZ + idx] * t[c * TSZ + idx];
     }
   };
+  // CONV: the FP32 copy of the slots this thread copied
+  auto convert_slots = [&](int slot) {
+    const TS* t = xs + slot * NF * TSZ;
+    T* o = xcv + slot * NC * TSZ;
+#pragma unroll
+    for (int j = 0; j < NSLOT; ++j) {
+      if (!(s_flags & (1u << (2 * j)))) continue;
+      const int idx = tid + j * NT;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) o[c * TSZ + idx] = (T)t[c * TSZ + idx];
+    }
+  };
   auto tile_val = [&](const TS* t, int c, int li) -> T {
     if (MODE == ST_CHEB_PRE && c < 3) return (T)t[(6 + c) * TSZ + li];
     return (T)t[c * TSZ + li];
@@ -219,6 +243,10 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
       if (k == zs) convert_plane(rk);
       if (k + 1 <= n) convert_plane(rk1);
     }
+    if constexpr (CONV) {
+      if (k == zs) convert_slots(rk);
+      if (k + 1 <= n) convert_slots(rk1);
+    }
     __syncthreads();
     {
       const TS* tl = xs + rk * NF * TSZ;
@@ -228,8 +256,13 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
         const int li = (ty + (q >> 1)) * TW + tx + (q & 1);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          if (k == zs) Xl[q][c] = tile_val(tl, c, li);
-          Xh[q][c] = (k + 1 <= n) ? tile_val(th, c, li) : T(0);
+          if constexpr (CONV) {
+            if (k == zs) Xl[q][c] = xcv[(rk * NC + c) * TSZ + li];
+            Xh[q][c] = (k + 1 <= n) ? xcv[(rk1 * NC + c) * TSZ + li] : T(0);
+          } else {
+            if (k == zs) Xl[q][c] = tile_val(tl, c, li);
+            Xh[q][c] = (k + 1 <= n) ? tile_val(th, c, li) : T(0);
+          }
         }
       }
       if (MODE == ST_CHEB_PRE && inner) {  // own b and D^-1 on plane k, before the ring slot is reused
