@@ -285,6 +285,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--batch", action="store_true", help="also run the 24-problem batch")
     ap.add_argument("--batch-n", type=int, default=0)
+    ap.add_argument("--solve-iters", type=int, default=0,
+                    help="profiling aid: run only K MINRES iterations of the workload's mixed solve "
+                         "inside the NVTX range 'solve', print one short JSON line and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -314,6 +317,19 @@ def main():
         t_tune = time.perf_counter()
         tuned = ctx.autotune(reps=10) if not args.no_tune else {}
         t_tune = time.perf_counter() - t_tune
+        if args.solve_iters > 0:
+            b = ctx.load_vector(fbar)
+            stream.synchronize()
+            torch.cuda.nvtx.range_push("solve")
+            try:
+                _, its, rel = ctx.solve(b, 1e-8, args.solve_iters)
+            except pkg.AgcaError as e:  # stopped at the iteration limit above the tolerance
+                its, rel = args.solve_iters, str(e)
+            stream.synchronize()
+            torch.cuda.nvtx.range_pop()
+            if rank == 0:
+                print(json.dumps({"solve_iters": its, "relres": rel}), flush=True)
+            return 0
         n3 = 3 * ctx.V[L]
         g = torch.Generator(device=dev)
         g.manual_seed(1234 + rank)
