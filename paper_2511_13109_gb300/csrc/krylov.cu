@@ -13,12 +13,6 @@ namespace {
 constexpr int kRedBlocks = 1216;  // 8 per SM; fixed so reductions are deterministic
 constexpr int kRedThreads = 256;
 
-// Vectors of the Krylov solver are read and written as 16-byte pairs when
-// every pointer of a kernel is 16-byte aligned (workspace vectors always are),
-// with the odd last entry done separately; each entry's arithmetic is the
-// same either way.
-__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
 struct DotPairs {
   const double* x[3];
   const double* y[3];
@@ -30,29 +24,9 @@ __global__ void __launch_bounds__(kRedThreads) dot_partial_kernel(DotPairs p, in
   double acc[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) acc[j] = 0.0;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  bool vec = true;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-  for (int j = 0; j < NP; ++j) vec = vec && al16(p.x[j]) && al16(p.y[j]);
-  if (vec) {
-    for (int64_t i = t0; i < (n >> 1); i += st) {
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const double2 a = reinterpret_cast<const double2*>(p.x[j])[i];
-        const double2 b = reinterpret_cast<const double2*>(p.y[j])[i];
-        acc[j] = fma(a.x, b.x, acc[j]);
-        acc[j] = fma(a.y, b.y, acc[j]);
-      }
-    }
-    if (t0 == 0 && (n & 1)) {
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc[j] = fma(p.x[j][n - 1], p.y[j][n - 1], acc[j]);
-    }
-  } else {
-    for (int64_t i = t0; i < n; i += st) {
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc[j] = fma(p.x[j][i], p.y[j][i], acc[j]);
-    }
+    for (int j = 0; j < NP; ++j) acc[j] = fma(p.x[j][i], p.y[j][i], acc[j]);
   }
   __shared__ double red[NP][kRedThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -137,22 +111,8 @@ __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const d
   const double ig = 1.0 / g;
   const double delta = kzz * ig * ig;  // z is kept unnormalized: z = gamma * zhat
   const double a = delta * ig, b = g / go;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  if (al16(kz) && al16(v) && al16(vold_to_vnew)) {
-    const double2* kz2 = reinterpret_cast<const double2*>(kz);
-    const double2* v2 = reinterpret_cast<const double2*>(v);
-    double2* o2 = reinterpret_cast<double2*>(vold_to_vnew);
-    for (int64_t i = t0; i < (n >> 1); i += st) {
-      const double2 p = kz2[i], q = v2[i];
-      double2 r = o2[i];
-      r.x = p.x * ig - a * q.x - b * r.x;
-      r.y = p.y * ig - a * q.y - b * r.y;
-      o2[i] = r;
-    }
-    if (t0 == 0 && (n & 1)) vold_to_vnew[n - 1] = kz[n - 1] * ig - a * v[n - 1] - b * vold_to_vnew[n - 1];
-  } else {
-    for (int64_t i = t0; i < n; i += st) vold_to_vnew[i] = kz[i] * ig - a * v[i] - b * vold_to_vnew[i];
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vold_to_vnew[i] = kz[i] * ig - a * v[i] - b * vold_to_vnew[i];
 }
 
 // red: the partials of z_new . v_new (summed here by the whole block) or nullptr
@@ -202,27 +162,10 @@ __global__ void minres_update_kernel(int64_t n, const double* __restrict__ z, co
   if (sc[MS_UPD_SKIP] != 0.0) return;
   const double ig = sc[MS_INV_GAMMA_PREV], a1 = sc[MS_A1], a2 = sc[MS_A2], a3 = sc[MS_A3], xc = sc[MS_XCOEF];
   const double ia1 = 1.0 / a1;
-  auto one = [&](double zi, double woi, double wi, double xi, double& wn, double& xn) {
-    wn = (zi * ig - a3 * woi - a2 * wi) * ia1;
-    xn = fma(xc, wn, xi);
-  };
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  if (al16(z) && al16(w) && al16(wold_to_wnew) && al16(x)) {
-    const double2* z2 = reinterpret_cast<const double2*>(z);
-    const double2* w2 = reinterpret_cast<const double2*>(w);
-    double2* o2 = reinterpret_cast<double2*>(wold_to_wnew);
-    double2* x2 = reinterpret_cast<double2*>(x);
-    for (int64_t i = t0; i < (n >> 1); i += st) {
-      const double2 zz = z2[i], ww = w2[i];
-      double2 oo = o2[i], xx = x2[i];
-      one(zz.x, oo.x, ww.x, xx.x, oo.x, xx.x);
-      one(zz.y, oo.y, ww.y, xx.y, oo.y, xx.y);
-      o2[i] = oo;
-      x2[i] = xx;
-    }
-    if (t0 == 0 && (n & 1)) one(z[n - 1], wold_to_wnew[n - 1], w[n - 1], x[n - 1], wold_to_wnew[n - 1], x[n - 1]);
-  } else {
-    for (int64_t i = t0; i < n; i += st) one(z[i], wold_to_wnew[i], w[i], x[i], wold_to_wnew[i], x[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (z[i] * ig - a3 * wold_to_wnew[i] - a2 * w[i]) * ia1;
+    wold_to_wnew[i] = wn;
+    x[i] = fma(xc, wn, x[i]);
   }
 }
 
