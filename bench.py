@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -315,7 +316,8 @@ def main():
         ctx = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
         ctx.prepare(eta, prm["nu"])
         t_tune = time.perf_counter()
-        tuned = ctx.autotune(reps=10) if not args.no_tune else {}
+        tune_cache = os.path.join(tempfile.mkdtemp(prefix="agca_bench_"), "tiles.txt")
+        tuned = ctx.autotune(reps=10, cache=tune_cache) if not args.no_tune else {}
         t_tune = time.perf_counter() - t_tune
         if args.solve_iters > 0:
             b = ctx.load_vector(fbar)
@@ -435,6 +437,8 @@ def main():
                     t0 = time.perf_counter()
                     c = pkg.Context(N, L, prec, device=dev, stream=stream)
                     c.prepare(eta, prm["nu"])
+                    if prec == pkg.MIXED and not args.no_tune:
+                        c.autotune(10, tune_cache)  # tile shapes read back from the cycle's tuning run
                     b = c.load_vector(fbar)
                     torch.cuda.synchronize(dev)
                     t1 = time.perf_counter()
