@@ -10,7 +10,11 @@ namespace agca {
 
 namespace {
 
-constexpr int kRedBlocks = 1216;  // 8 per SM; fixed so reductions are deterministic
+constexpr int kRedBlocks = 1216;  // 8 per SM: grid of the streaming vector kernels
+// blocks (= partial sums) of a reduction: 4 per SM, fixed so reductions are
+// deterministic, and few enough that a consumer kernel's blocks can each sum
+// them cheaply
+constexpr int kRedParts = 608;
 constexpr int kRedThreads = 256;
 
 struct DotPairs {
@@ -102,7 +106,7 @@ __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const d
   if (sc[MS_DONE] != 0.0) return;
   double kzz;
   if (red) {
-    kzz = block_sum(red, kRedBlocks);
+    kzz = block_sum(red, kRedParts);
     if (blockIdx.x == 0 && threadIdx.x == 0) sc[MS_DOT_KZZ] = kzz;
   } else {
     kzz = sc[MS_DOT_KZZ];
@@ -118,7 +122,7 @@ __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const d
 // red: the partials of z_new . v_new (summed here by the whole block) or nullptr
 __global__ void minres_scalar_kernel(double* sc, const double* red) {
   grid_dep_entry();
-  const double zv = red ? block_sum(red, kRedBlocks) : 0.0;
+  const double zv = red ? block_sum(red, kRedParts) : 0.0;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (red) sc[MS_DOT_ZV] = zv;
   if (sc[MS_DONE] != 0.0) return;
@@ -192,7 +196,7 @@ __global__ void minres_init_kernel(double* sc, double tol_rel) {
 __global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
                               const double* scal, const double* red, double red_scale) {
   grid_dep_entry();
-  const double s0 = red ? red_scale * block_sum(red, kRedBlocks) : (scal ? scal[0] : 0.0);
+  const double s0 = red ? red_scale * block_sum(red, kRedParts) : (scal ? scal[0] : 0.0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     switch (op) {
       case VOP_SUB: y[i] = a[i] - b[i]; break;            // y = a - b
@@ -300,7 +304,7 @@ cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int dot_blocks() { return kRedBlocks; }
+int dot_blocks() { return kRedParts; }
 
 cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
                         double* out, double scale, cudaStream_t s) {
@@ -310,12 +314,12 @@ cudaError_t launch_dots(int npairs, const double* const* xs, const double* const
     p.y[j] = ys[j];
   }
   switch (npairs) {
-    case 1: KL(launch_k(dot_partial_kernel<1>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
-    case 2: KL(launch_k(dot_partial_kernel<2>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
-    case 3: KL(launch_k(dot_partial_kernel<3>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 1: KL(launch_k(dot_partial_kernel<1>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 2: KL(launch_k(dot_partial_kernel<2>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 3: KL(launch_k(dot_partial_kernel<3>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
     default: return cudaErrorInvalidValue;
   }
-  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, npairs, out, scale));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedParts, npairs, out, scale));
   return cudaGetLastError();
 }
 
@@ -323,18 +327,18 @@ cudaError_t launch_dot_partials(const double* x, const double* y, int64_t n, dou
   DotPairs p{};
   p.x[0] = x;
   p.y[0] = y;
-  KL(launch_k(dot_partial_kernel<1>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials));
+  KL(launch_k(dot_partial_kernel<1>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_partials(const double* x, int64_t n, double* partials, cudaStream_t s) {
-  KL(launch_k(sum_partial_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, x, n, partials));
+  KL(launch_k(sum_partial_kernel, dim3(kRedParts), dim3(kRedThreads), 0, s, x, n, partials));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s) {
-  KL(launch_k(sum_partial_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, x, n, partials));
-  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, 1, out, scale));
+  KL(launch_k(sum_partial_kernel, dim3(kRedParts), dim3(kRedThreads), 0, s, x, n, partials));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedParts, 1, out, scale));
   return cudaGetLastError();
 }
 
