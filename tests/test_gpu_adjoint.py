@@ -72,3 +72,36 @@ def test_adjoint_matches_finite_differences(prec):
         ad = float(torch.dot(g, d))
         assert abs(fd - ad) <= 1e-5 * abs(fd), (k, fd, ad)
     assert u0.shape == (n3,)
+
+
+def test_adjoint_full_size_finite_differences():
+    """The adjoint benchmark workload (64^3 pressure cubes, 8 spheres, jump
+    1e4, observation from log-viscosity + N(0, 0.1^2)), mixed precision:
+    the autograd gradient against central finite differences of the forward
+    solve along seeded directions."""
+    from synth import adjoint_problem
+
+    N = 64
+    p, theta_obs = adjoint_problem(N)
+    fbar = torch.from_numpy(p.fbar.ravel()).to(DEV)
+    prob = pkg.StokesProblem(N, fbar, precision=pkg.MIXED, rtol=1e-10, device=DEV)
+    theta = torch.log(torch.from_numpy(p.eta).to(DEV))
+    with torch.no_grad():
+        u_obs = pkg.stokes_velocity(torch.from_numpy(theta_obs).to(DEV), prob).clone()
+
+    def J(th):
+        with torch.no_grad():
+            u = pkg.stokes_velocity(th, prob)
+            return 0.5 * float(torch.sum((u - u_obs) ** 2))
+
+    th = theta.clone().requires_grad_(True)
+    u = pkg.stokes_velocity(th, prob)
+    (0.5 * torch.sum((u - u_obs) ** 2)).backward()
+    g = th.grad.clone()
+    assert torch.isfinite(g).all()
+    eps = 1e-4
+    for k in range(3):
+        d = torch.from_numpy(np.random.default_rng(200 + k).normal(size=theta.numel())).to(DEV)
+        fd = (J(theta + eps * d) - J(theta - eps * d)) / (2 * eps)
+        ad = float(torch.dot(g, d))
+        assert abs(fd - ad) <= 1e-5 * abs(fd), (k, fd, ad)
