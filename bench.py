@@ -123,6 +123,15 @@ def _peaks():
         return {}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per finest-level
+# stencil launch of the 64^3 workload, mean over the four launches of one
+# V-cycle (pre-smoothing 110.4 MB, residual 107.6 MB, first post-smoothing step
+# 135.3 MB, last step with the FP64-widened result 179.6 MB), from one ncu
+# capture of the current kernel; the algorithmic bytes of the same launches
+# average 154.6 MB (part of the inputs is still in L2 from the previous launch)
+FINE_STENCIL_DRAM_BYTES = 133.2e6
+
+
 def bench_levels(N):
     """Levels of the benchmark hierarchy: coarsen the 2N velocity grid while
     it stays even with >= 4 cubes (the library's default)."""
@@ -469,7 +478,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": arm_config(N, L, flagged, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": FINE_STENCIL_DRAM_BYTES if N == 64 else None,
+                         "traffic_unit": "DRAM bytes per finest-level stencil launch (ncu)",
                          "kernel": "finest-level stencil (Chebyshev/residual epilogues), FP32",
                          "launches_timed": k_launches, "peak_source": "measured hbm_gbs"},
             "cpu_baseline": cpu,
