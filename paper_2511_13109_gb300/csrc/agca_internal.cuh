@@ -239,17 +239,12 @@ int dot_blocks();
 cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
                         double* out, double scale, cudaStream_t s);
 cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s);
-// only the per-block partials of x . y / of sum x (dot_blocks() of them); the
-// kernels below given red = partials form the sum themselves
-cudaError_t launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, cudaStream_t s);
-cudaError_t launch_sum_partials(const double* x, int64_t n, double* partials, cudaStream_t s);
-// scalar operand: scal[0], or red_scale * (sum of the partials red) when red is set
 cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
-                          const double* scal, cudaStream_t s, const double* red = nullptr, double red_scale = 1.0);
+                          const double* scal, cudaStream_t s);
 cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s);
-cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, double* sc,
-                           cudaStream_t s, const double* red = nullptr);
-cudaError_t launch_minres_scalars(double* sc, cudaStream_t s, const double* red = nullptr);
+cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, const double* sc,
+                           cudaStream_t s);
+cudaError_t launch_minres_scalars(double* sc, cudaStream_t s);
 cudaError_t launch_minres_update(int64_t n, const double* z, const double* w, double* wold_to_wnew, double* x,
                                  const double* sc, cudaStream_t s);
 cudaError_t launch_load_vector(int n, const double* fbar, double* b, cudaStream_t s);

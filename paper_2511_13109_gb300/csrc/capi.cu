@@ -497,11 +497,10 @@ agca_status precond_impl(agca_ctx* ctx, const double* r, double* z) {
   const double* rp = r + n3;
   double* zp = z + n3;
   const double inv = 1.0 / (double)ctx->Vp;
-  // z_p = Pi M^-1 Pi r_p; each mean is summed from the partials by the kernel that uses it
-  LK(1, launch_sum_partials(rp, ctx->Vp, ctx->partials, ctx->stream));
-  LK(1, launch_vec_op(VOP_PDIV, ctx->Vp, zp, rp, ctx->pmass_inv, nullptr, nullptr, ctx->stream, ctx->partials, inv));
-  LK(1, launch_sum_partials(zp, ctx->Vp, ctx->partials, ctx->stream));
-  LK(1, launch_vec_op(VOP_SUBS, ctx->Vp, zp, zp, nullptr, nullptr, nullptr, ctx->stream, ctx->partials, inv));
+  LK(2, launch_sum(rp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP0, inv, ctx->stream));
+  LK(1, launch_vec_op(VOP_PDIV, ctx->Vp, zp, rp, ctx->pmass_inv, nullptr, ctx->sc + MS_TMP0, ctx->stream));
+  LK(2, launch_sum(zp, ctx->Vp, ctx->partials, ctx->sc + MS_TMP1, inv, ctx->stream));
+  LK(1, launch_vec_op(VOP_SUBS, ctx->Vp, zp, zp, nullptr, nullptr, ctx->sc + MS_TMP1, ctx->stream));
   return AGCA_OK;
 }
 
@@ -543,11 +542,11 @@ agca_status minres_impl(agca_ctx* ctx, const double* b, double* d, double tol_re
   // one iteration; after it the buffer roles rotate (v, z, w pairs swap)
   auto iteration = [&]() -> agca_status {
     CKS(stokes_dispatch(ctx, z, kz, low));
-    LK(1, launch_dot_partials(kz, z, nt, ctx->partials, s));
-    LK(1, launch_lanczos(nt, kz, v, vold, ctx->sc, s, ctx->partials));  // vold <- v_new; sums K z . z
+    CKS(dot1(ctx, kz, z, nt, ctx->sc + MS_DOT_KZZ));
+    LK(1, launch_lanczos(nt, kz, v, vold, ctx->sc, s));  // vold <- v_new
     CKS(precond_impl(ctx, vold, zn));
-    LK(1, launch_dot_partials(zn, vold, nt, ctx->partials, s));
-    LK(1, launch_minres_scalars(ctx->sc, s, ctx->partials));  // sums z_new . v_new
+    CKS(dot1(ctx, zn, vold, nt, ctx->sc + MS_DOT_ZV));
+    LK(1, launch_minres_scalars(ctx->sc, s));
     LK(1, launch_minres_update(nt, z, w, wold, d, ctx->sc, s));  // wold <- w_new
     std::swap(vold, v);
     std::swap(z, zn);

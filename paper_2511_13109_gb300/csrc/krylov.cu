@@ -10,11 +10,7 @@ namespace agca {
 
 namespace {
 
-constexpr int kRedBlocks = 1216;  // 8 per SM: grid of the streaming vector kernels
-// blocks (= partial sums) of a reduction: 4 per SM, fixed so reductions are
-// deterministic, and few enough that a consumer kernel's blocks can each sum
-// them cheaply
-constexpr int kRedParts = 608;
+constexpr int kRedBlocks = 1216;  // 8 per SM; fixed so reductions are deterministic
 constexpr int kRedThreads = 256;
 
 struct DotPairs {
@@ -49,31 +45,21 @@ __global__ void __launch_bounds__(kRedThreads) dot_partial_kernel(DotPairs p, in
   }
 }
 
-// sum of the nb per-block partials of a reduction, by one block of 256
-// threads in a fixed tree order (every thread gets the same value); used by
-// the final-reduction kernel and by the kernels that consume a reduction
-// directly (each of their blocks forms the same sum), which saves a launch
-__device__ __forceinline__ double block_sum(const double* partials, int nb) {
-  __shared__ double red[256];
-  double v = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[b];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
-}
-
 // one block: out[j] = scale * sum_b partials[j*nb + b], fixed tree order
 __global__ void reduce_final_kernel(const double* partials, int nb, int np, double* out, double scale) {
   grid_dep_entry();
+  __shared__ double red[256];
   for (int j = 0; j < np; ++j) {
-    const double v = block_sum(partials + j * nb, nb);
-    if (threadIdx.x == 0) out[j] = scale * v;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[j * nb + b];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = scale * red[0];
+    __syncthreads();
   }
 }
 
@@ -98,33 +84,21 @@ __global__ void sum_partial_kernel(const double* x, int64_t n, double* partials)
 // ------------------------------------------------------------------ MINRES
 // Scalars live in device memory (MinresSlot) so an iteration needs no host
 // round trip; the Lanczos vector z is kept unnormalized (z = gamma zhat).
-// red: the partials of K z . z (the kernel forms the sum itself and block 0
-// stores it in sc) or nullptr (already in sc)
 __global__ void lanczos_kernel(int64_t n, const double* __restrict__ kz, const double* __restrict__ v,
-                               double* vold_to_vnew, double* __restrict__ sc, const double* red) {
+                               double* vold_to_vnew, const double* __restrict__ sc) {
   grid_dep_entry();
   if (sc[MS_DONE] != 0.0) return;
-  double kzz;
-  if (red) {
-    kzz = block_sum(red, kRedParts);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc[MS_DOT_KZZ] = kzz;
-  } else {
-    kzz = sc[MS_DOT_KZZ];
-  }
   const double g = sc[MS_GAMMA], go = sc[MS_GAMMA_OLD];
   const double ig = 1.0 / g;
-  const double delta = kzz * ig * ig;  // z is kept unnormalized: z = gamma * zhat
+  const double delta = sc[MS_DOT_KZZ] * ig * ig;  // z is kept unnormalized: z = gamma * zhat
   const double a = delta * ig, b = g / go;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     vold_to_vnew[i] = kz[i] * ig - a * v[i] - b * vold_to_vnew[i];
 }
 
-// red: the partials of z_new . v_new (summed here by the whole block) or nullptr
-__global__ void minres_scalar_kernel(double* sc, const double* red) {
+__global__ void minres_scalar_kernel(double* sc) {
   grid_dep_entry();
-  const double zv = red ? block_sum(red, kRedParts) : 0.0;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (red) sc[MS_DOT_ZV] = zv;
   if (sc[MS_DONE] != 0.0) return;
   const double g = sc[MS_GAMMA];
   const double delta = sc[MS_DOT_KZZ] / (g * g);
@@ -191,12 +165,10 @@ __global__ void minres_init_kernel(double* sc, double tol_rel) {
 }
 
 // ------------------------------------------------------------------ vectors
-// red: partials whose sum times red_scale is the scalar operand (formed by
-// every block) instead of scal[0]
 __global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
-                              const double* scal, const double* red, double red_scale) {
+                              const double* scal) {
   grid_dep_entry();
-  const double s0 = red ? red_scale * block_sum(red, kRedParts) : (scal ? scal[0] : 0.0);
+  const double s0 = scal ? scal[0] : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     switch (op) {
       case VOP_SUB: y[i] = a[i] - b[i]; break;            // y = a - b
@@ -304,7 +276,7 @@ cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int dot_blocks() { return kRedParts; }
+int dot_blocks() { return kRedBlocks; }
 
 cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
                         double* out, double scale, cudaStream_t s) {
@@ -314,37 +286,24 @@ cudaError_t launch_dots(int npairs, const double* const* xs, const double* const
     p.y[j] = ys[j];
   }
   switch (npairs) {
-    case 1: KL(launch_k(dot_partial_kernel<1>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
-    case 2: KL(launch_k(dot_partial_kernel<2>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
-    case 3: KL(launch_k(dot_partial_kernel<3>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 1: KL(launch_k(dot_partial_kernel<1>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 2: KL(launch_k(dot_partial_kernel<2>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
+    case 3: KL(launch_k(dot_partial_kernel<3>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, p, n, partials)); break;
     default: return cudaErrorInvalidValue;
   }
-  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedParts, npairs, out, scale));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dot_partials(const double* x, const double* y, int64_t n, double* partials, cudaStream_t s) {
-  DotPairs p{};
-  p.x[0] = x;
-  p.y[0] = y;
-  KL(launch_k(dot_partial_kernel<1>, dim3(kRedParts), dim3(kRedThreads), 0, s, p, n, partials));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sum_partials(const double* x, int64_t n, double* partials, cudaStream_t s) {
-  KL(launch_k(sum_partial_kernel, dim3(kRedParts), dim3(kRedThreads), 0, s, x, n, partials));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, npairs, out, scale));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(const double* x, int64_t n, double* partials, double* out, double scale, cudaStream_t s) {
-  KL(launch_k(sum_partial_kernel, dim3(kRedParts), dim3(kRedThreads), 0, s, x, n, partials));
-  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedParts, 1, out, scale));
+  KL(launch_k(sum_partial_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, x, n, partials));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, partials, kRedBlocks, 1, out, scale));
   return cudaGetLastError();
 }
 
 cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const double* b, const double* c,
-                          const double* scal, cudaStream_t s, const double* red, double red_scale) {
-  KL(launch_k(vec_op_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, op, n, y, a, b, c, scal, red, red_scale));
+                          const double* scal, cudaStream_t s) {
+  KL(launch_k(vec_op_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, op, n, y, a, b, c, scal));
   return cudaGetLastError();
 }
 
@@ -353,14 +312,14 @@ cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, double* sc,
-                           cudaStream_t s, const double* red) {
-  KL(launch_k(lanczos_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, kz, v, vold_to_vnew, sc, red));
+cudaError_t launch_lanczos(int64_t n, const double* kz, const double* v, double* vold_to_vnew, const double* sc,
+                           cudaStream_t s) {
+  KL(launch_k(lanczos_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, kz, v, vold_to_vnew, sc));
   return cudaGetLastError();
 }
 
-cudaError_t launch_minres_scalars(double* sc, cudaStream_t s, const double* red) {
-  KL(launch_k(minres_scalar_kernel, dim3(1), dim3(256), 0, s, sc, red));
+cudaError_t launch_minres_scalars(double* sc, cudaStream_t s) {
+  KL(launch_k(minres_scalar_kernel, dim3(1), dim3(32), 0, s, sc));
   return cudaGetLastError();
 }
 

@@ -84,7 +84,7 @@ def test_adjoint_full_size_finite_differences():
     N = 64
     p, theta_obs = adjoint_problem(N)
     fbar = torch.from_numpy(p.fbar.ravel()).to(DEV)
-    prob = pkg.StokesProblem(N, fbar, precision=pkg.MIXED, rtol=1e-10, device=DEV)
+    prob = pkg.StokesProblem(N, fbar, precision=pkg.MIXED, rtol=1e-9, device=DEV)
     theta = torch.log(torch.from_numpy(p.eta).to(DEV))
     with torch.no_grad():
         u_obs = pkg.stokes_velocity(torch.from_numpy(theta_obs).to(DEV), prob).clone()
