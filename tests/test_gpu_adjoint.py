@@ -78,7 +78,10 @@ def test_adjoint_full_size_finite_differences():
     """The adjoint benchmark workload (64^3 pressure cubes, 8 spheres, jump
     1e4, observation from log-viscosity + N(0, 0.1^2)), mixed precision:
     the autograd gradient against central finite differences of the forward
-    solve along seeded directions."""
+    solve along seeded directions.  With forward and adjoint solves to a
+    1e-9 relative residual and eps = 1e-4, the solves' errors enter the
+    central difference at a few 1e-5 relative, so agreement is asserted to
+    1e-4 (the 8^3 check above solves to 1e-12 and asserts 1e-5)."""
     from synth import adjoint_problem
 
     N = 64
@@ -104,4 +107,4 @@ def test_adjoint_full_size_finite_differences():
         d = torch.from_numpy(np.random.default_rng(200 + k).normal(size=theta.numel())).to(DEV)
         fd = (J(theta + eps * d) - J(theta - eps * d)) / (2 * eps)
         ad = float(torch.dot(g, d))
-        assert abs(fd - ad) <= 1e-5 * abs(fd), (k, fd, ad)
+        assert abs(fd - ad) <= 1e-4 * abs(fd), (k, fd, ad)
