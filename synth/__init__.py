@@ -12,6 +12,7 @@ from .sinkers import (  # noqa: F401
     element_quadrature_points,
     cube_sinker,
     sphere_sinkers,
+    sphere_sinkers_on_device,
     gaussian_logbumps,
     batch_problems,
     adjoint_problem,

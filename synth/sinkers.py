@@ -106,6 +106,23 @@ def _element_means(N: int, field_fn, rule: str, device, ncomp: int):
     return eta, fbar
 
 
+def _element_means_on_device(N: int, field_fn, device):
+    """As _element_means (4-point rule, one forcing component), with the
+    results left on the device: (eta (E,), fbar (3, E)) float64 tensors.
+    For grids whose host copies would be tens of GB."""
+    n = velocity_grid(N)
+    per_layer = 6 * n * n
+    eta = torch.empty(6 * n ** 3, dtype=torch.float64, device=device)
+    fbar = torch.zeros((3, 6 * n ** 3), dtype=torch.float64, device=device)
+    nk = max(1, min(n, (8 << 20) // (per_layer * 4)))
+    for k0 in range(0, n, nk):
+        k1 = min(n, k0 + nk)
+        e, f = field_fn(element_quadrature_points(n, k0, k1, "quad4", device))
+        eta[k0 * per_layer:k1 * per_layer] = e.mean(dim=-1).reshape(-1)
+        fbar[2, k0 * per_layer:k1 * per_layer] = f.mean(dim=-1).reshape(-1)
+    return eta, fbar
+
+
 def _device(device):
     if device == "auto":
         return "cuda" if torch.cuda.is_available() else "cpu"
@@ -151,6 +168,17 @@ def sphere_sinkers(N: int, n_sinkers: int = 8, radius: float = 0.08, width: floa
     eta, fbar = _element_means(N, fn, "quad4", _device(device), 1)
     return Problem(N, eta, fbar, dict(kind="spheres", centres=centres, radius=radius,
                                       width=width, dr=dr, seed=seed))
+
+
+def sphere_sinkers_on_device(N: int, n_sinkers: int = 8, radius: float = 0.08, width: float = 0.01,
+                             dr: float = 1e6, seed: int = CONFIG_SEED0 + 1, device="cuda"):
+    """The sphere_sinkers field family generated and kept on the device:
+    (eta, fbar, centres) with eta (E,) and fbar (3, E) float64 tensors."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.2, 0.8, size=(n_sinkers, 3))
+    fn = _tanh_spheres_fn(centres, np.full(n_sinkers, radius), width, dr)
+    eta, fbar = _element_means_on_device(N, fn, device)
+    return eta, fbar, centres
 
 
 def gaussian_logbumps(N: int, n_bumps: int = 20, seed: int = CONFIG_SEED0 + 2,
