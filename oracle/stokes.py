@@ -147,11 +147,12 @@ class Stokes:
         dofs = fem.element_dofs(self.vm)
         return np.einsum("ei,eij,ej->e", lam_u[dofs], Ke, u[dofs])
 
-    def adjoint_gradient(self, x, u_obs, solver="direct"):
+    def adjoint_gradient(self, x, u_obs, solver="direct", rtol=1e-13):
         """dJ/dtheta for J = 0.5 ||u - u_obs||^2: solve K lambda = (u - u_obs, 0)
-        (K symmetric), then g_e = -lambda_e^T (dA_e/dtheta_e) u_e."""
+        (K symmetric), then g_e = -lambda_e^T (dA_e/dtheta_e) u_e.  solver:
+        "direct" (sparse LU) or MINRES to the relative residual rtol."""
         u = x[:self.nu_]
         rhs = np.zeros_like(x)
         rhs[:self.nu_] = (u - u_obs) * self.mask
-        lam = self.direct(rhs) if solver == "direct" else self.solve(rhs, 1e-13)[0]
+        lam = self.direct(rhs) if solver == "direct" else self.solve(rhs, rtol)[0]
         return -self.element_sensitivity(lam[:self.nu_], u)
