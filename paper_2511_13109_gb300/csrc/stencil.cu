@@ -47,12 +47,28 @@ __host__ __device__ constexpr int stencil_tile_fields() {
   return MODE == ST_CHEB_PRE ? 9 : (MODE == ST_STOKES ? 4 : 3);
 }
 
-// dynamic shared memory of one block: tile ring [3][NF][(BX+1)(BY+1)] of TS,
-// then (128-byte aligned, as the 8/16-byte async copies need) the
-// coefficient ring [2][BX*BY][6] of T and the y-exchange [2][NC][BX*BY] of T
+// FP32 tiles keep the operator input of a vertex as one float4 (its 3 or 4
+// components), so a corner is one 16-byte shared load and the y-exchange one
+// 16-byte store and load per cube layer; FP64 tiles keep one array per field
+template <typename TS>
+__host__ __device__ constexpr bool stencil_aos() {
+  return sizeof(TS) == 4;
+}
+// TS elements of one ring slot: AoS [4 * TSZ] (+ CHEB_PRE: b and D^-1 as
+// [6][TSZ], padded to whole float4s), or SoA [NF][TSZ]
+template <typename TS, int BX, int BY, int MODE>
+__host__ __device__ constexpr int stencil_slot_elems() {
+  constexpr int TSZ = (BX + 1) * (BY + 1);
+  return stencil_aos<TS>() ? 4 * TSZ + (MODE == ST_CHEB_PRE ? (6 * TSZ + 3) / 4 * 4 : 0)
+                           : stencil_tile_fields<MODE, TS>() * TSZ;
+}
+
+// dynamic shared memory of one block: tile ring [3][slot] of TS, then
+// (128-byte aligned, as the 8/16-byte async copies need) the coefficient ring
+// [2][BX*BY][6] of T and the y-exchange ([2][BX*BY][4] AoS or [2][NC][BX*BY]) of T
 template <typename TS, int BX, int BY, int MODE>
 __host__ __device__ constexpr size_t stencil_tile_bytes() {
-  return ((size_t)3 * stencil_tile_fields<MODE, TS>() * (BX + 1) * (BY + 1) * sizeof(TS) + 127) / 128 * 128;
+  return ((size_t)3 * stencil_slot_elems<TS, BX, BY, MODE>() * sizeof(TS) + 127) / 128 * 128;
 }
 // Stokes operator with FP64 vectors and FP32 arithmetic: every staged value
 // is converted once, by the thread that copied it, into an FP32 copy of the
@@ -67,7 +83,7 @@ template <typename TS, typename T, int BX, int BY, int MODE>
 __host__ __device__ constexpr size_t stencil_smem_bytes() {
   constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;
   return stencil_tile_bytes<TS, BX, BY, MODE>() + (size_t)2 * BX * BY * 6 * sizeof(T) +
-         (size_t)2 * NC * BX * BY * sizeof(T) +
+         (size_t)2 * (stencil_aos<TS>() ? 4 : NC) * BX * BY * sizeof(T) +
          (stencil_converts<TS, T, MODE>() ? (size_t)3 * NC * (BX + 1) * (BY + 1) * sizeof(T) : 0);
 }
 
@@ -86,10 +102,13 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   constexpr int NF = stencil_tile_fields<MODE, TS>();
   constexpr int TW = BX + 1, TSZ = (BX + 1) * (BY + 1), NT = BX * BY;
   constexpr int NSLOT = (TSZ + NT - 1) / NT;
+  constexpr bool AOS = stencil_aos<TS>();
+  constexpr int SS = stencil_slot_elems<TS, BX, BY, MODE>();
   TS* xs = reinterpret_cast<TS*>(smem_raw);
   T* cfs = reinterpret_cast<T*>(smem_raw + stencil_tile_bytes<TS, BX, BY, MODE>());
   T* cs = cfs + 2 * NT * 6;
   constexpr bool CONV = stencil_converts<TS, T, MODE>();
+  static_assert(!(AOS && CONV), "an FP32 tile needs no conversion");
   T* xcv = cs + 2 * NC * NT;  // CONV: FP32 ring [3][NC][TSZ]
 
   // 32-bit indices: the host limits grids to 3 (n+1)^3 < 2^31 and 6 n^3 < 2^31
@@ -127,7 +146,8 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   const int zs = z0 - 1;
   // plane z goes to ring slot `slot` (plane zs + i uses slot i mod 3)
   auto issue_tile = [&](int z, int slot) {
-    TS* dst = xs + slot * NF * TSZ;
+    TS* dst = xs + slot * SS;
+    TS* soa = AOS ? dst + 4 * TSZ : dst;  // CHEB_PRE: b, D^-1
     const bool zin = (z > 0) && (z < n);
     const bool zq = (z >= 0) && (z <= n);
     const int pb = z * plane;
@@ -140,15 +160,16 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (MODE == ST_CHEB_PRE) {
-          cp_async(dst + c * TSZ + idx, a.b + (c * V + v), sizeof(TS), in);
-          cp_async(dst + (3 + c) * TSZ + idx, a.invD + (c * V + v), sizeof(TS), in);
+          cp_async(soa + c * TSZ + idx, a.b + (c * V + v), sizeof(TS), in);
+          cp_async(soa + (3 + c) * TSZ + idx, a.invD + (c * V + v), sizeof(TS), in);
         } else {
-          cp_async(dst + c * TSZ + idx, a.x + (c * V + v), sizeof(TS), in);
+          cp_async(AOS ? dst + 4 * idx + c : dst + c * TSZ + idx, a.x + (c * V + v), sizeof(TS), in);
         }
       }
       if (MODE == ST_STOKES) {  // fine-grid pressure q = P p lives on every vertex
         const bool qin = zq && (s_flags & (1u << (16 + j)));
-        cp_async(dst + 3 * TSZ + idx, a.q + (qin ? pb + s_col[j] : 0), sizeof(TS), qin);
+        cp_async(AOS ? dst + 4 * idx + 3 : dst + 3 * TSZ + idx, a.q + (qin ? pb + s_col[j] : 0), sizeof(TS),
+                 qin);
       }
     }
   };
@@ -167,18 +188,25 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   // CHEB_PRE: the first Chebyshev iterate x1 = s2 D^-1 b of the slots this
   // thread copied, formed once in shared memory (fields 6..8)
   auto convert_plane = [&](int slot) {
-    TS* t = xs + slot * NF * TSZ;
+    TS* t = xs + slot * SS;
+    const TS* soa = AOS ? t + 4 * TSZ : t;
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
       if (!(s_flags & (1u << (2 * j)))) continue;
       const int idx = tid + j * NT;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) t[(6 + c) * TSZ + idx] = a.s2 * t[(3 + c) * TSZ + idx] * t[c * TSZ + idx];
+      for (int c = 0; c < 3; ++c) {
+        const TS x1 = a.s2 * soa[(3 + c) * TSZ + idx] * soa[c * TSZ + idx];
+        if constexpr (AOS)
+          t[4 * idx + c] = x1;
+        else
+          t[(6 + c) * TSZ + idx] = x1;
+      }
     }
   };
   // CONV: the FP32 copy of the slots this thread copied
   auto convert_slots = [&](int slot) {
-    const TS* t = xs + slot * NF * TSZ;
+    const TS* t = xs + slot * SS;
     T* o = xcv + slot * NC * TSZ;
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
@@ -191,6 +219,19 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
   auto tile_val = [&](const TS* t, int c, int li) -> T {
     if (MODE == ST_CHEB_PRE && c < 3) return (T)t[(6 + c) * TSZ + li];
     return (T)t[c * TSZ + li];
+  };
+  // the NC operator-input components of tile vertex li of a ring slot
+  auto load_vertex = [&](const TS* t, int li, T (&v)[NC]) {
+    if constexpr (AOS) {
+      const float4 q = *reinterpret_cast<const float4*>(t + 4 * li);
+      v[0] = q.x;
+      v[1] = q.y;
+      v[2] = q.z;
+      if constexpr (NC == 4) v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = tile_val(t, c, li);
+    }
   };
 
   // prologue: planes zs, zs+1 and the coefficients of cube layer zs
@@ -249,28 +290,34 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     }
     __syncthreads();
     {
-      const TS* tl = xs + rk * NF * TSZ;
-      const TS* th = xs + rk1 * NF * TSZ;
+      const TS* tl = xs + rk * SS;
+      const TS* th = xs + rk1 * SS;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int li = (ty + (q >> 1)) * TW + tx + (q & 1);
+        if constexpr (CONV) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          if constexpr (CONV) {
+          for (int c = 0; c < NC; ++c) {
             if (k == zs) Xl[q][c] = xcv[(rk * NC + c) * TSZ + li];
             Xh[q][c] = (k + 1 <= n) ? xcv[(rk1 * NC + c) * TSZ + li] : T(0);
+          }
+        } else {
+          if (k == zs) load_vertex(tl, li, Xl[q]);
+          if (k + 1 <= n) {
+            load_vertex(th, li, Xh[q]);
           } else {
-            if (k == zs) Xl[q][c] = tile_val(tl, c, li);
-            Xh[q][c] = (k + 1 <= n) ? tile_val(th, c, li) : T(0);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Xh[q][c] = T(0);
           }
         }
       }
       if (MODE == ST_CHEB_PRE && inner) {  // own b and D^-1 on plane k, before the ring slot is reused
         const int li = (ty + 1) * TW + tx + 1;
+        const TS* soa = AOS ? tl + 4 * TSZ : tl;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          eb[c] = tl[c * TSZ + li];
-          ed[c] = tl[(3 + c) * TSZ + li];
+          eb[c] = soa[c * TSZ + li];
+          ed[c] = soa[(3 + c) * TSZ + li];
         }
       }
     }
@@ -326,23 +373,47 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     // combine along x (lane tx+1 holds the neighbouring cube), then along y
     T s1[2][NC];
 #pragma unroll
-    for (int qz = 0; qz < 2; ++qz)
+    for (int qz = 0; qz < 2; ++qz) {
+      T s0[4];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         // corners (qx, qy, qz): index qx + 2 qy + 4 qz
         const T from_right_y1 = __shfl_down_sync(0xffffffffu, Y[4 * qz + 2][c], 1);
         const T from_right_y0 = __shfl_down_sync(0xffffffffu, Y[4 * qz + 0][c], 1);
-        s1[qz][c] = Y[4 * qz + 3][c] + from_right_y1;                        // row qy = 1 (own vertex row)
-        cs[((qz & 1) * NC + c) * NT + tid] = Y[4 * qz + 1][c] + from_right_y0;  // row qy = 0, for thread ty-1
+        s1[qz][c] = Y[4 * qz + 3][c] + from_right_y1;  // row qy = 1 (own vertex row)
+        s0[c] = Y[4 * qz + 1][c] + from_right_y0;      // row qy = 0, for thread ty-1
       }
+      if constexpr (AOS) {
+        reinterpret_cast<float4*>(cs)[qz * NT + tid] = make_float4(s0[0], s0[1], s0[2], NC == 4 ? s0[3] : 0.f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cs[(qz * NC + c) * NT + tid] = s0[c];
+      }
+    }
     __syncthreads();
 
     if (owner) {
+      T up[2][4];  // row qy = 0 sums of the cube above, per qz
+      if constexpr (AOS) {
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz) {
+          const float4 u = reinterpret_cast<const float4*>(cs)[qz * NT + tid + BX];
+          up[qz][0] = u.x;
+          up[qz][1] = u.y;
+          up[qz][2] = u.z;
+          up[qz][3] = u.w;
+        }
+      } else {
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) up[qz][c] = cs[(qz * NC + c) * NT + tid + BX];
+      }
       T yk[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        yk[c] = acc[c] + (s1[0][c] + cs[c * NT + tid + BX]);
-        acc[c] = s1[1][c] + cs[(NC + c) * NT + tid + BX];
+        yk[c] = acc[c] + (s1[0][c] + up[0][c]);
+        acc[c] = s1[1][c] + up[1][c];
       }
       if (out_k) {
 #pragma unroll
