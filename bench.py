@@ -125,11 +125,11 @@ def _peaks():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per finest-level
 # stencil launch of the 64^3 workload, mean over the four launches of one
-# V-cycle (pre-smoothing 110.4 MB, residual 107.6 MB, first post-smoothing step
-# 135.3 MB, last step with the FP64-widened result 179.6 MB), from one ncu
+# V-cycle (pre-smoothing 109.8 MB, residual 106.0 MB, first post-smoothing step
+# 135.0 MB, last step with the FP64-widened result 183.2 MB), from one ncu
 # capture of the current kernel; the algorithmic bytes of the same launches
 # average 154.6 MB (part of the inputs is still in L2 from the previous launch)
-FINE_STENCIL_DRAM_BYTES = 133.2e6
+FINE_STENCIL_DRAM_BYTES = 133.5e6
 
 
 def bench_levels(N):
