@@ -216,6 +216,16 @@ agca_status agca_tile_config(const agca_ctx* ctx, int level, int mode, int* by, 
  * not depend on the tile shape: every vertex sums its element contributions
  * in the same order.  Host only; AGCA_EINVAL for other values. */
 agca_status agca_set_tile_config(agca_ctx* ctx, int level, int mode, int by, int zch);
+/* The tile grid the stencil kernels use on a grid of n cubes per axis with
+ * by block rows and z-chunk request zch (0 = automatic): out[0..6] = wide
+ * strips in x, wide tile rows in y, narrow strips in x, narrow tile rows in
+ * y, first vertex column of the narrow strips, z-chunks, vertex planes per
+ * z-chunk.  Wide tiles own 31 x (by - 1) vertex columns x rows, narrow tiles
+ * 7 x (4 by - 1); every vertex of the (n+1)^2 plane is owned by exactly one
+ * tile and every vertex plane by exactly one z-chunk.  out is a host array
+ * of 7 ints.  Host only, no context; AGCA_EINVAL for n < 1, n > 1024, by not
+ * 8, 12 or 16, or zch < 0. */
+agca_status agca_stencil_tiles(int n, int by, int zch, int* out);
 
 /* Number of CUDA kernels this context has launched so far (host counter). */
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);

@@ -25,6 +25,7 @@ from .agca import (  # noqa: F401
     default_levels,
     exported_symbols,
     lib,
+    stencil_tiles,
     stokes_apply_static,
 )
 from .adjoint import StokesProblem, stokes_velocity  # noqa: F401,E402

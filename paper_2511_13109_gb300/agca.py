@@ -67,6 +67,7 @@ _SIGS = {
     "agca_autotune": ([_P, _I, ctypes.c_char_p], _I),
     "agca_tile_config": ([_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "agca_set_tile_config": ([_P, _I, _I, _I, _I], _I),
+    "agca_stencil_tiles": ([_I, _I, _I, ctypes.POINTER(_I)], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
@@ -105,6 +106,17 @@ def lib():
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def stencil_tiles(n: int, block_rows: int = 8, z_chunk: int = 0) -> dict:
+    """Tile grid of the stencil kernels on a grid of n cubes per axis (see
+    agca_stencil_tiles in include/agca.h)."""
+    out = (_I * 7)()
+    st = lib().agca_stencil_tiles(int(n), int(block_rows), int(z_chunk), out)
+    if st != 0:
+        raise AgcaError(st, f"agca_stencil_tiles(n={n}, by={block_rows}, zch={z_chunk})")
+    keys = ("gxw", "gyw", "gxn", "gyn", "x0n", "gz", "zch")
+    return dict(zip(keys, list(out)))
 
 
 def default_levels(N: int) -> int:

@@ -1525,6 +1525,14 @@ agca_status agca_set_tile_config(agca_ctx* ctx, int level, int mode, int by, int
   return AGCA_OK;
 }
 
+agca_status agca_stencil_tiles(int n, int by, int zch, int* out) {
+  if (!out || n < 1 || n > 1024 || !(by == 8 || by == 12 || by == 16) || zch < 0) return AGCA_EINVAL;
+  const TileGrid g = stencil_tiles(n, by, zch);
+  const int v[7] = {g.gxw, g.gyw, g.gxn, g.gyn, g.x0n, g.gz, g.zch};
+  for (int i = 0; i < 7; ++i) out[i] = v[i];
+  return AGCA_OK;
+}
+
 agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches) {
   if (!ctx || !launches) return AGCA_EINVAL;
   *launches = ctx->launches;
