@@ -10,7 +10,11 @@ elements it covers vary by more than the threshold:
 Flagged elements store A_e^GCA = sum_k (I3 x p_k)^T C_k (I3 x p_k) over their
 8 children (Eqs. 2.6-2.7, Eq. B.2), where C_k is the child's finest matrix,
 its stored Galerkin matrix, or its direct (DCA, Eq. 2.5) matrix built from
-the arithmetic mean of the child's viscosity.  Unflagged elements use DCA.
+the arithmetic mean of the child's viscosity (or its harmonic or geometric
+mean: the P0 projections of Sec. 3.2).  Unflagged elements use DCA.
+gradient_flags gives the paper's own flag rule (Eq. 2.8: gradient norm of
+the P1-interpolated viscosity above nu), with coarse elements in the role of
+macro elements.
 The level operator is the heterogeneous sum of Eq. 2.9.
 
 The V-cycle uses Chebyshev smoothing on D^-1 A (Section 4, degree 2 by
@@ -52,10 +56,50 @@ def pairwise8(c: np.ndarray) -> np.ndarray:
            ((c[..., 4] + c[..., 5]) + (c[..., 6] + c[..., 7]))
 
 
+PROJECTIONS = ("arithmetic", "harmonic", "geometric")
+
+
+def coarse_mean(c: np.ndarray, projection: str = "arithmetic") -> np.ndarray:
+    """Piecewise-constant (P0) coefficient of a parent from its 8 children's
+    values c[..., 8]: the arithmetic, harmonic or geometric mean, the three
+    P0 projections of Sec. 3.2 (Fig. 6).  Sums run in the pairwise8 order."""
+    if projection == "arithmetic":
+        return pairwise8(c) * 0.125
+    if projection == "harmonic":
+        return 8.0 / pairwise8(1.0 / c)
+    if projection == "geometric":
+        return np.exp(pairwise8(np.log(c)) * 0.125)
+    raise ValueError(f"unknown projection {projection!r}")
+
+
+def gradient_norms(mesh: Mesh, eta_v: np.ndarray) -> np.ndarray:
+    """Per element of mesh, the norm of the gradient of the P1 interpolant
+    with nodal values eta_v (the quantity Eq. 2.8 thresholds), from the
+    element's barycentric gradients."""
+    g = np.einsum("ea,eai->ei", np.asarray(eta_v, dtype=np.float64)[mesh.tets], mesh.grads)
+    return np.sqrt(np.einsum("ei,ei->e", g, g))
+
+
+def gradient_flags(N: int, L: int, eta_v: np.ndarray, nu: float):
+    """The flag rule of Eq. 2.8 with the level-l element in the role of the
+    macro element: flag it iff the gradient norm of the P1 interpolant of
+    the viscosity (nodal values eta_v on the finest grid) exceeds nu on at
+    least one finest element it covers.  Returns (gmax, flags) keyed by
+    level; gmax[L] holds the finest elements' norms."""
+    nL = 2 * N
+    gmax = {L: gradient_norms(Mesh(nL), eta_v)}
+    flags = {}
+    for l in range(L - 1, 0, -1):
+        k = children_n(nL >> (L - l))
+        gmax[l] = gmax[l + 1][k].max(axis=1)
+        flags[l] = gmax[l] > nu
+    return gmax, flags
+
+
 class Hierarchy:
     def __init__(self, N: int, L: int, eta: np.ndarray, nu: float = 10.0,
                  cheb_lo: float = 0.1, cheb_hi: float = 1.1, cheb_degree: int = 2,
-                 power_iters: int = 20, build_operators: bool = True):
+                 power_iters: int = 20, build_operators: bool = True, projection: str = "arithmetic"):
         nL = 2 * N
         assert nL % (1 << (L - 1)) == 0 and (nL >> (L - 1)) >= 2
         self.N, self.L, self.nu = N, L, nu
@@ -69,7 +113,7 @@ class Hierarchy:
         self.mean, self.mx, self.mn, self.flags = {L: eta}, {L: eta}, {L: eta}, {}
         for l in range(L - 1, 0, -1):
             k = self.ch[l]
-            self.mean[l] = pairwise8(self.mean[l + 1][k]) * 0.125
+            self.mean[l] = coarse_mean(self.mean[l + 1][k], projection)
             self.mx[l] = self.mx[l + 1][k].max(axis=1)
             self.mn[l] = self.mn[l + 1][k].min(axis=1)
             self.flags[l] = self.mx[l] > nu * self.mn[l]
@@ -207,14 +251,14 @@ class Hierarchy:
         return float(self.flags[l].mean())
 
 
-def flag_hierarchy(N: int, L: int, eta: np.ndarray, nu: float):
+def flag_hierarchy(N: int, L: int, eta: np.ndarray, nu: float, projection: str = "arithmetic"):
     """Viscosity hierarchy and flags only (cheap at any size): dicts
     mean, mx, mn, flags keyed by level, plus the children maps."""
     nL = 2 * N
     mean, mx, mn, flags = {L: eta}, {L: eta}, {L: eta}, {}
     for l in range(L - 1, 0, -1):
         k = children_n(nL >> (L - l))
-        mean[l] = pairwise8(mean[l + 1][k]) * 0.125
+        mean[l] = coarse_mean(mean[l + 1][k], projection)
         mx[l] = mx[l + 1][k].max(axis=1)
         mn[l] = mn[l + 1][k].min(axis=1)
         flags[l] = mx[l] > nu * mn[l]

@@ -1,0 +1,116 @@
+"""Pins of the oracle's coefficient variants: the three P0 projections of the
+coarse coefficient (arithmetic, harmonic, geometric mean, Sec. 3.2 / Fig. 6)
+and the paper's gradient-norm flag rule (Eq. 2.8), each checked against
+closed forms and invariants that do not reuse the oracle's formulas."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import agca
+from oracle.mesh import PERMS, Mesh, children_n
+
+
+def test_projections_of_two_valued_children():
+    a, b = 3.0, 7000.0
+    for pos in itertools.combinations(range(8), 4):  # every arrangement of 4 a's and 4 b's
+        c = np.full(8, b)
+        c[list(pos)] = a
+        assert agca.coarse_mean(c, "arithmetic") == pytest.approx((a + b) / 2, rel=1e-15)
+        assert agca.coarse_mean(c, "harmonic") == pytest.approx(2 * a * b / (a + b), rel=1e-15)
+        assert agca.coarse_mean(c, "geometric") == pytest.approx(np.sqrt(a * b), rel=1e-15)
+    c = np.full(8, 0.37)
+    assert agca.coarse_mean(c, "arithmetic") == 0.37
+    for p in ("harmonic", "geometric"):
+        assert agca.coarse_mean(c, p) == pytest.approx(0.37, rel=2e-16)
+    with pytest.raises(ValueError):
+        agca.coarse_mean(c, "median")
+
+
+@pytest.mark.parametrize("projection", agca.PROJECTIONS)
+def test_projection_equals_mean_over_finest_descendants(projection):
+    """The recursion over levels equals the same mean taken over all finest
+    descendants at once (equal weights), and HM <= GM <= AM."""
+    N, L = 4, 3
+    eta = np.exp(np.random.default_rng(3).normal(0.0, 2.0, 6 * (2 * N) ** 3))
+    mean, mx, mn, _ = agca.flag_hierarchy(N, L, eta, 10.0, projection)
+    nL = 2 * N
+    desc = np.arange(len(eta))[:, None]  # finest descendants of each level-L element
+    for l in range(L - 1, 0, -1):
+        desc = desc[children_n(nL >> (L - l))].reshape(6 * (nL >> (L - l)) ** 3, -1)
+        v = eta[desc]
+        want = {"arithmetic": v.mean(axis=1), "harmonic": 1.0 / (1.0 / v).mean(axis=1),
+                "geometric": np.exp(np.log(v).mean(axis=1))}[projection]
+        assert np.allclose(mean[l], want, rtol=1e-13, atol=0)
+        assert (mean[l] <= mx[l] * (1 + 1e-14)).all() and (mean[l] >= mn[l] * (1 - 1e-14)).all()
+    am = agca.flag_hierarchy(N, L, eta, 10.0, "arithmetic")[0]
+    gm = agca.flag_hierarchy(N, L, eta, 10.0, "geometric")[0]
+    hm = agca.flag_hierarchy(N, L, eta, 10.0, "harmonic")[0]
+    for l in range(1, L):
+        assert (hm[l] <= gm[l] * (1 + 1e-13)).all() and (gm[l] <= am[l] * (1 + 1e-13)).all()
+
+
+@pytest.mark.parametrize("projection", ["harmonic", "geometric"])
+def test_dca_equals_gca_for_constant_viscosity_any_projection(projection):
+    """Sec. 2.1: for a constant coefficient the rediscretised and Galerkin
+    coarse operators coincide; every projection of a constant is the constant."""
+    N, L = 2, 2
+    eta = np.full(6 * (2 * N) ** 3, 4.5)
+    h_dca = agca.Hierarchy(N, L, eta, nu=1e30, projection=projection)   # nothing flagged
+    h_gca = agca.Hierarchy(N, L, eta, nu=-1.0, projection=projection)   # everything flagged
+    A, B = h_dca.A[1].toarray(), h_gca.A[1].toarray()
+    assert np.abs(A - B).max() <= 1e-12 * np.abs(A).max()
+
+
+def test_gradient_norm_of_linear_field():
+    """The P1 interpolant of a linear function is the function: its gradient
+    is the constant vector on every element."""
+    n = 6
+    m = Mesh(n)
+    a = np.array([3.0, -40.0, 12.5])
+    eta_v = m.coords @ a + 2.0
+    g = agca.gradient_norms(m, eta_v)
+    assert np.allclose(g, np.linalg.norm(a), rtol=1e-12, atol=0)
+    N, L = n // 2, 2
+    _, flags = agca.gradient_flags(N, L, eta_v, 0.99 * np.linalg.norm(a))
+    assert flags[1].all()
+    _, flags = agca.gradient_flags(N, L, eta_v, 1.01 * np.linalg.norm(a))
+    assert not flags[1].any()
+
+
+def test_gradient_norm_from_kuhn_path_differences():
+    """On a Kuhn tetrahedron with path permutation p the P1 gradient has
+    component p[k] equal to the difference of the nodal values along the
+    k-th path edge divided by h (the edges are axis-parallel)."""
+    n = 4
+    m = Mesh(n)
+    eta_v = np.random.default_rng(5).uniform(0.5, 2.0, m.nv)
+    g = np.zeros((m.ne, 3))
+    for e in range(m.ne):
+        p = PERMS[e % 6]
+        v = m.tets[e]
+        for k in range(3):
+            g[e, p[k]] = (eta_v[v[k + 1]] - eta_v[v[k]]) * n
+    assert np.allclose(agca.gradient_norms(m, eta_v), np.linalg.norm(g, axis=1), rtol=1e-12, atol=0)
+
+
+def test_gradient_flags_of_a_step():
+    """Nodal values 1 left of x = 1/2 and 1000 from it on: only the cubes of
+    the column just left of the step have vertices on both sides (each of
+    their tetrahedra joins the cube origin to the opposite corner), with
+    gradient norm 999 n; every coarse element covering that column is
+    flagged, no other."""
+    N, L = 4, 3
+    nL = 2 * N
+    m = Mesh(nL)
+    eta_v = np.where(m.ijk[:, 0] < nL // 2, 1.0, 1000.0)
+    gmax, flags = agca.gradient_flags(N, L, eta_v, 10.0)
+    col = (np.arange(m.ne) // 6) % nL
+    crossing = col == nL // 2 - 1
+    assert np.allclose(gmax[L][crossing], 999.0 * nL, rtol=1e-12) and not gmax[L][~crossing].any()
+    for l in range(1, L):
+        nl = nL >> (L - l)
+        ccol = (np.arange(6 * nl ** 3) // 6) % nl
+        want = ccol == (nL // 2 - 1) >> (L - l)
+        assert np.array_equal(flags[l], want)
+        assert flags[l].sum() == 6 * nl * nl
