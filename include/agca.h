@@ -109,6 +109,14 @@ agca_status agca_set_smoother(agca_ctx* ctx, int degree, double lo, double hi, i
  * between host-side convergence checks (default 4). */
 agca_status agca_set_solver_options(agca_ctx* ctx, double mixed_inner_rtol, int check_every);
 
+/* Coarse DCA coefficient of a coarse element from its 8 children's values
+ * (Sec. 3.2, Fig. 6: the piecewise-constant projections): 0 = arithmetic
+ * mean (default), 1 = harmonic mean 8 / sum(1/c_k), 2 = geometric mean
+ * exp(sum(log c_k) / 8), sums in the fixed pairwise order
+ * ((c0+c1)+(c2+c3))+((c4+c5)+(c6+c7)).  Takes effect at the next agca_flag.
+ * Host only; AGCA_EINVAL for another kind. */
+agca_status agca_set_coarse_projection(agca_ctx* ctx, int kind);
+
 /* Bytes of device workspace the context needs (excluding the Galerkin store). */
 agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes);
 /* Bind caller-owned device memory of at least agca_workspace_size bytes,

@@ -19,6 +19,9 @@ from .agca import (  # noqa: F401
     FIELD_PMASS,
     FP64,
     MIXED,
+    PROJ_ARITHMETIC,
+    PROJ_GEOMETRIC,
+    PROJ_HARMONIC,
     AgcaError,
     Batch,
     Context,

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libagca.so")
 
 FP64, MIXED = 0, 1
 F64, F32 = 0, 1
+PROJ_ARITHMETIC, PROJ_HARMONIC, PROJ_GEOMETRIC = 0, 1, 2
 FIELD_MEAN, FIELD_MAX, FIELD_MIN, FIELD_FLAGS, FIELD_LIST, FIELD_GCA, FIELD_DIAG, FIELD_COARSE, FIELD_PMASS = range(9)
 
 STATUS = {0: "AGCA_OK", 1: "AGCA_EINVAL", 2: "AGCA_ENOMEM", 3: "AGCA_ECUDA", 4: "AGCA_ENOTCONV",
@@ -68,6 +69,7 @@ _SIGS = {
     "agca_tile_config": ([_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "agca_set_tile_config": ([_P, _I, _I, _I, _I], _I),
     "agca_stencil_tiles": ([_I, _I, _I, ctypes.POINTER(_I)], _I),
+    "agca_set_coarse_projection": ([_P, _I], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
@@ -223,6 +225,11 @@ class Context:
     def set_solver_options(self, mixed_inner_rtol: float = 1e-4, check_every: int = 4):
         self._check(lib().agca_set_solver_options(self._h, float(mixed_inner_rtol), int(check_every)),
                     "set_solver_options")
+
+    def set_coarse_projection(self, kind: int):
+        """Coarse coefficient as the children's arithmetic (PROJ_ARITHMETIC),
+        harmonic (PROJ_HARMONIC) or geometric (PROJ_GEOMETRIC) mean; before flag()."""
+        self._check(lib().agca_set_coarse_projection(self._h, int(kind)), "set_coarse_projection")
 
     def set_viscosity(self, eta: torch.Tensor):
         _need(eta, self.E[self.L], torch.float64, "eta")

@@ -204,8 +204,9 @@ cudaError_t launch_prolong(int nf, int ncomp, bool mask, bool add, const T* ec, 
 
 // setup kernels (setup.cu)
 cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStream_t s);
-cudaError_t launch_coarsen(int nc, const double* mean_f, const double* mx_f, const double* mn_f, double nu,
-                           double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s);
+// projection: coarse coefficient as the children's arithmetic (0), harmonic (1) or geometric (2) mean
+cudaError_t launch_coarsen(int nc, int projection, const double* mean_f, const double* mx_f, const double* mn_f,
+                           double nu, double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s);
 cudaError_t launch_compact(const uint8_t* flags, int64_t n, int32_t* fidx, int32_t* list, int32_t* block_counts,
                            int64_t* total, cudaStream_t s);
 int64_t compact_scratch_blocks(int64_t n);

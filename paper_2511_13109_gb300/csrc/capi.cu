@@ -63,6 +63,7 @@ struct agca_ctx {
   double cheb_lo = 0.1, cheb_hi = 1.1;
   int power_iters = 20;
   double mixed_inner = 1e-4;  // floor of the inner MINRES tolerance in mixed refinement
+  int projection = 0;         // coarse DCA coefficient: 0 arithmetic, 1 harmonic, 2 geometric mean
   int check_every = 4;        // MINRES iterations between host convergence checks
   std::vector<Level> lev;  // 1..L
   // workspace
@@ -1256,6 +1257,13 @@ agca_status agca_set_solver_options(agca_ctx* ctx, double mixed_inner_rtol, int 
   return AGCA_OK;
 }
 
+agca_status agca_set_coarse_projection(agca_ctx* ctx, int kind) {
+  if (!ctx) return AGCA_EINVAL;
+  if (kind < 0 || kind > 2) return ctx->fail(AGCA_EINVAL, "projection must be 0, 1 or 2");
+  ctx->projection = kind;
+  return AGCA_OK;
+}
+
 agca_status agca_workspace_size(const agca_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return AGCA_EINVAL;
   *bytes = ctx->ws_need;
@@ -1300,7 +1308,7 @@ agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
   for (int l = L - 1; l >= 1; --l) {
     Level& lc = ctx->lev[l];
     const Level& lf = ctx->lev[l + 1];
-    LK(1, launch_coarsen(lc.n, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
+    LK(1, launch_coarsen(lc.n, ctx->projection, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
   }
   for (int l = 1; l < L; ++l) {
     Level& lc = ctx->lev[l];

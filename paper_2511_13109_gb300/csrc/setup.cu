@@ -26,7 +26,8 @@ __device__ __forceinline__ int64_t child_id(const RefineTables& rt, int nf, int 
   return 6 * ((2 * I + c[0]) + (int64_t)nf * ((2 * J + c[1]) + (int64_t)nf * (2 * K + c[2]))) + c[3];
 }
 
-__global__ void coarsen_kernel(const RefineTables rt, int nc, const double* __restrict__ mean_f, const double* __restrict__ mx_f,
+__global__ void coarsen_kernel(const RefineTables rt, int nc, int projection, const double* __restrict__ mean_f,
+                               const double* __restrict__ mx_f,
                                const double* __restrict__ mn_f, double nu, double* __restrict__ mean_c,
                                double* __restrict__ mx_c, double* __restrict__ mn_c, uint8_t* __restrict__ flags) {
   grid_dep_entry();
@@ -46,10 +47,19 @@ __global__ void coarsen_kernel(const RefineTables rt, int nc, const double* __re
     hi = k == 0 ? a : fmax(hi, a);
     lo = k == 0 ? b : fmin(lo, b);
   }
-  // fixed pairwise order, no contraction possible (additions only), exact /8
+  // P0 projection of the children (Sec. 3.2): the arithmetic, harmonic or
+  // geometric mean, summed in a fixed pairwise order with explicit roundings
+  // (no contraction), /8 exact
+  if (projection == 1) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = __ddiv_rn(1.0, m[k]);
+  } else if (projection == 2) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = log(m[k]);
+  }
   const double s = __dadd_rn(__dadd_rn(__dadd_rn(m[0], m[1]), __dadd_rn(m[2], m[3])),
                              __dadd_rn(__dadd_rn(m[4], m[5]), __dadd_rn(m[6], m[7])));
-  mean_c[e] = s * 0.125;
+  mean_c[e] = projection == 1 ? __ddiv_rn(8.0, s) : (projection == 2 ? exp(s * 0.125) : s * 0.125);
   mx_c[e] = hi;
   mn_c[e] = lo;
   flags[e] = hi > __dmul_rn(nu, lo) ? 1 : 0;
@@ -394,11 +404,11 @@ cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarsen(int nc, const double* mean_f, const double* mx_f, const double* mn_f, double nu,
-                           double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s) {
+cudaError_t launch_coarsen(int nc, int projection, const double* mean_f, const double* mx_f, const double* mn_f,
+                           double nu, double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s) {
   const int64_t E = nelems(nc);
   KL(launch_k(coarsen_kernel, dim3(blocks_for(E, 256)), dim3(256), 0, s,
-     refine_tables(), nc, mean_f, mx_f, mn_f, nu, mean_c, mx_c, mn_c, flags));
+     refine_tables(), nc, projection, mean_f, mx_f, mn_f, nu, mean_c, mx_c, mn_c, flags));
   return cudaGetLastError();
 }
 

@@ -58,6 +58,8 @@ def test_host_only_calls(libagca):
     assert L.agca_set_solver_options(h, 0.0, 4) == 1
     assert L.agca_set_solver_options(h, 1e-4, 0) == 1
     assert L.agca_set_solver_options(h, 1e-4, 8) == 0
+    assert L.agca_set_coarse_projection(h, 3) == 1 and L.agca_set_coarse_projection(h, -1) == 1
+    assert L.agca_set_coarse_projection(h, 2) == 0 and L.agca_set_coarse_projection(h, 0) == 0
     assert L.agca_set_tile_config(h, 2, 1, 8, 5) == 0
     assert L.agca_set_tile_config(h, 2, 1, 12, 0) == 1   # 12 block rows: FP32 cycle launches only
     assert L.agca_set_tile_config(h, 0, 1, 8, 0) == 1
