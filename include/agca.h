@@ -135,6 +135,14 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev);
  * every coarse level in ascending id order.  Returns in *gca_bytes the size
  * of the Galerkin store to bind next.  Synchronizes. */
 agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes);
+/* As agca_flag, with the paper's own flag rule (Eq. 2.8) at element
+ * granularity: a coarse element is flagged iff the norm of the gradient of
+ * the P1 interpolant of the viscosity exceeds nu on at least one finest
+ * element it covers.  eta_vertex_dev: the viscosity at the finest-grid
+ * vertices (double[V_L], device, vertex order as for vectors, every value
+ * finite and > 0; read during the call only).  The hierarchy of means,
+ * maxima and minima is built as by agca_flag.  Synchronizes. */
+agca_status agca_flag_gradient(agca_ctx* ctx, const double* eta_vertex_dev, double nu, size_t* gca_bytes);
 /* Bind caller-owned device memory for the stored Galerkin matrices. */
 agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes);
 

@@ -99,7 +99,8 @@ def gradient_flags(N: int, L: int, eta_v: np.ndarray, nu: float):
 class Hierarchy:
     def __init__(self, N: int, L: int, eta: np.ndarray, nu: float = 10.0,
                  cheb_lo: float = 0.1, cheb_hi: float = 1.1, cheb_degree: int = 2,
-                 power_iters: int = 20, build_operators: bool = True, projection: str = "arithmetic"):
+                 power_iters: int = 20, build_operators: bool = True, projection: str = "arithmetic",
+                 eta_vertex: np.ndarray | None = None):
         nL = 2 * N
         assert nL % (1 << (L - 1)) == 0 and (nL >> (L - 1)) >= 2
         self.N, self.L, self.nu = N, L, nu
@@ -117,6 +118,8 @@ class Hierarchy:
             self.mx[l] = self.mx[l + 1][k].max(axis=1)
             self.mn[l] = self.mn[l + 1][k].min(axis=1)
             self.flags[l] = self.mx[l] > nu * self.mn[l]
+        if eta_vertex is not None:  # the gradient rule of Eq. 2.8 instead of the ratio rule
+            self.flags = gradient_flags(N, L, eta_vertex, nu)[1]
         self.flist = {l: np.nonzero(self.flags[l])[0] for l in range(1, L)}
         self.findex = {}
         for l in range(1, L):

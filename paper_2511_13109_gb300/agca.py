@@ -70,6 +70,7 @@ _SIGS = {
     "agca_set_tile_config": ([_P, _I, _I, _I, _I], _I),
     "agca_stencil_tiles": ([_I, _I, _I, ctypes.POINTER(_I)], _I),
     "agca_set_coarse_projection": ([_P, _I], _I),
+    "agca_flag_gradient": ([_P, _P, _D, ctypes.POINTER(_SZ)], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
@@ -238,6 +239,16 @@ class Context:
     def flag(self, nu: float) -> int:
         b = _SZ()
         self._check(lib().agca_flag(self._h, float(nu), ctypes.byref(b)), "flag")
+        self.gca_store = torch.empty(int(b.value), dtype=torch.uint8, device=self.device)
+        self._check(lib().agca_bind_gca_store(self._h, _ptr(self.gca_store), b.value), "bind_gca_store")
+        return int(b.value)
+
+    def flag_gradient(self, eta_vertex: torch.Tensor, nu: float) -> int:
+        """Flags by the gradient rule of Eq. 2.8 from the finest nodal
+        viscosity (see agca_flag_gradient); binds the Galerkin store."""
+        _need(eta_vertex, self.V[self.L], torch.float64, "eta_vertex")
+        b = _SZ()
+        self._check(lib().agca_flag_gradient(self._h, _ptr(eta_vertex), float(nu), ctypes.byref(b)), "flag_gradient")
         self.gca_store = torch.empty(int(b.value), dtype=torch.uint8, device=self.device)
         self._check(lib().agca_bind_gca_store(self._h, _ptr(self.gca_store), b.value), "bind_gca_store")
         return int(b.value)

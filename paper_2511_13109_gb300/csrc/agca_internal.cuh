@@ -204,6 +204,11 @@ cudaError_t launch_prolong(int nf, int ncomp, bool mask, bool add, const T* ec, 
 
 // setup kernels (setup.cu)
 cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStream_t s);
+// Eq. 2.8 flags of a coarse level (nc cubes): from the finest nodal viscosity
+// eta_v when given (the level above the finest), else from the flags of the
+// next finer level flags_f
+cudaError_t launch_gradient_flags(int nc, const double* eta_v, double nu, const uint8_t* flags_f, uint8_t* flags_c,
+                                  cudaStream_t s);
 // projection: coarse coefficient as the children's arithmetic (0), harmonic (1) or geometric (2) mean
 cudaError_t launch_coarsen(int nc, int projection, const double* mean_f, const double* mx_f, const double* mn_f,
                            double nu, double* mean_c, double* mx_c, double* mn_c, uint8_t* flags, cudaStream_t s);

@@ -1294,7 +1294,10 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
   return AGCA_OK;
 }
 
-agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
+namespace {
+// viscosity hierarchy and flags: by the element-wise ratio rule, or (eta_v
+// set) by the gradient rule of Eq. 2.8 on the finest nodal viscosity
+agca_status flag_impl(agca_ctx* ctx, double nu, const double* eta_v, size_t* gca_bytes) {
   if (!ctx || !gca_bytes) return AGCA_EINVAL;
   ctx->clear_graphs();
   if (!ctx->have_eta) return ctx->fail(AGCA_ESTATE, "set the viscosity first");
@@ -1303,12 +1306,16 @@ agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
   const int L = ctx->L;
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), s));
   LK(1, launch_check_eta(ctx->lev[L].mean, ctx->lev[L].E, ctx->status, s));
+  if (eta_v) LK(1, launch_check_eta(eta_v, ctx->lev[L].V, ctx->status, s));
   CKS(check_status(ctx, "agca_flag"));
   ctx->nu = nu;
   for (int l = L - 1; l >= 1; --l) {
     Level& lc = ctx->lev[l];
     const Level& lf = ctx->lev[l + 1];
     LK(1, launch_coarsen(lc.n, ctx->projection, lf.mean, lf.mx, lf.mn, nu, lc.mean, lc.mx, lc.mn, lc.flags, s));
+    if (eta_v)
+      LK(1, launch_gradient_flags(lc.n, l == L - 1 ? eta_v : nullptr, nu, l == L - 1 ? nullptr : lf.flags, lc.flags,
+                                  s));
   }
   for (int l = 1; l < L; ++l) {
     Level& lc = ctx->lev[l];
@@ -1324,6 +1331,14 @@ agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) {
   ctx->setup_done = false;
   ctx->gs = nullptr;
   return AGCA_OK;
+}
+}  // namespace
+
+agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) { return flag_impl(ctx, nu, nullptr, gca_bytes); }
+
+agca_status agca_flag_gradient(agca_ctx* ctx, const double* eta_vertex_dev, double nu, size_t* gca_bytes) {
+  if (!eta_vertex_dev) return ctx ? ctx->fail(AGCA_EINVAL, "nodal viscosity missing") : AGCA_EINVAL;
+  return flag_impl(ctx, nu, eta_vertex_dev, gca_bytes);
 }
 
 agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes) {

@@ -65,6 +65,66 @@ __global__ void coarsen_kernel(const RefineTables rt, int nc, int projection, co
   flags[e] = hi > __dmul_rn(nu, lo) ? 1 : 0;
 }
 
+// Eq. 2.8 on finest element (cube (i, j, k), type t) of a grid of n cubes:
+// the norm of the gradient of the P1 interpolant of the nodal viscosity
+// eta_v.  The element's path edges are axis-parallel, so gradient component
+// perm(t, m) is the difference of the nodal values along the m-th path edge
+// times n.  Explicit roundings, IEEE square root.
+__device__ __forceinline__ double gradient_norm(const double* __restrict__ eta_v, int n, int i, int j, int k, int t) {
+  const int64_t nv = n + 1;
+  double prev = eta_v[i + nv * (j + nv * (int64_t)k)], s = 0.0;
+  int q = 0;  // cube-corner bits of the current path vertex
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    q |= 1 << perm(t, m);
+    const double cur = eta_v[(i + (q & 1)) + nv * ((j + ((q >> 1) & 1)) + nv * (int64_t)(k + ((q >> 2) & 1)))];
+    const double d = __dmul_rn(__dsub_rn(cur, prev), (double)n);
+    s = __dadd_rn(s, __dmul_rn(d, d));
+    prev = cur;
+  }
+  return __dsqrt_rn(s);
+}
+
+// flags of the level above the finest grid: an element is flagged iff the
+// gradient norm exceeds nu on one of its 8 finest children
+__global__ void gradient_flag_kernel(const RefineTables rt, int nc, const double* __restrict__ eta_v, double nu,
+                                     uint8_t* __restrict__ flags) {
+  grid_dep_entry();
+  const int64_t E = nelems(nc);
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int t = (int)(e % 6);
+  const int64_t cube = e / 6;
+  const int I = (int)(cube % nc), J = (int)((cube / nc) % nc), K = (int)(cube / ((int64_t)nc * nc));
+  const int nf = 2 * nc;
+  bool f = false;
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int64_t c = child_id(rt, nf, I, J, K, t, k);
+    const int64_t cc = c / 6;
+    const int ci = (int)(cc % nf), cj = (int)((cc / nf) % nf), ck = (int)(cc / ((int64_t)nf * nf));
+    f = f || gradient_norm(eta_v, nf, ci, cj, ck, (int)(c % 6)) > nu;
+  }
+  flags[e] = f ? 1 : 0;
+}
+
+// coarser levels: flagged iff one of the 8 children is (the maximum over the
+// finest descendants exceeds nu)
+__global__ void flag_children_kernel(const RefineTables rt, int nc, const uint8_t* __restrict__ flags_f,
+                                     uint8_t* __restrict__ flags_c) {
+  grid_dep_entry();
+  const int64_t E = nelems(nc);
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int t = (int)(e % 6);
+  const int64_t cube = e / 6;
+  const int I = (int)(cube % nc), J = (int)((cube / nc) % nc), K = (int)(cube / ((int64_t)nc * nc));
+  uint8_t f = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f |= flags_f[child_id(rt, 2 * nc, I, J, K, t, k)];
+  flags_c[e] = f ? 1 : 0;
+}
+
 constexpr int kCompactChunk = 1024;  // elements per block (256 threads x 4)
 
 __global__ void compact_count_kernel(const uint8_t* flags, int64_t n, int32_t* counts) {
@@ -401,6 +461,18 @@ inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) /
 
 cudaError_t launch_check_eta(const double* eta, int64_t n, int* status, cudaStream_t s) {
   KL(launch_k(check_eta_kernel, dim3(1216), dim3(256), 0, s, eta, n, status));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_flags(int nc, const double* eta_v, double nu, const uint8_t* flags_f, uint8_t* flags_c,
+                                  cudaStream_t s) {
+  const int64_t E = nelems(nc);
+  if (eta_v)
+    KL(launch_k(gradient_flag_kernel, dim3(blocks_for(E, 256)), dim3(256), 0, s, refine_tables(), nc, eta_v, nu,
+                flags_c));
+  else
+    KL(launch_k(flag_children_kernel, dim3(blocks_for(E, 256)), dim3(256), 0, s, refine_tables(), nc, flags_f,
+                flags_c));
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@ from .sinkers import (  # noqa: F401
     cube_sinker,
     sphere_sinkers,
     sphere_sinkers_on_device,
+    sphere_sinkers_vertex,
     gaussian_logbumps,
     batch_problems,
     adjoint_problem,

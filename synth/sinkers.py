@@ -181,6 +181,21 @@ def sphere_sinkers_on_device(N: int, n_sinkers: int = 8, radius: float = 0.08, w
     return eta, fbar, centres
 
 
+def sphere_sinkers_vertex(N: int, n_sinkers: int = 8, radius: float = 0.08, width: float = 0.01,
+                          dr: float = 1e6, seed: int = CONFIG_SEED0 + 1) -> np.ndarray:
+    """The sphere_sinkers viscosity at the vertices of the finest grid (the
+    nodal values of its P1 interpolant), float64 in vertex order
+    i + (n+1)(j + (n+1)k)."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.2, 0.8, size=(n_sinkers, 3))
+    fn = _tanh_spheres_fn(centres, np.full(n_sinkers, radius), width, dr)
+    n = velocity_grid(N)
+    g = torch.arange(n + 1, dtype=torch.float64) / n
+    K, J, I = torch.meshgrid(g, g, g, indexing="ij")
+    eta, _ = fn(torch.stack([I, J, K], dim=-1))
+    return eta.reshape(-1).numpy()
+
+
 def gaussian_logbumps(N: int, n_bumps: int = 20, seed: int = CONFIG_SEED0 + 2,
                       device="cpu") -> Problem:
     """Smooth log10-viscosity: sum of Gaussian bumps, clipped to [-3, 3];

@@ -58,6 +58,7 @@ def test_host_only_calls(libagca):
     assert L.agca_set_solver_options(h, 0.0, 4) == 1
     assert L.agca_set_solver_options(h, 1e-4, 0) == 1
     assert L.agca_set_solver_options(h, 1e-4, 8) == 0
+    assert L.agca_flag_gradient(h, None, ctypes.c_double(1.0), ctypes.byref(sz)) == 1  # nodal viscosity missing
     assert L.agca_set_coarse_projection(h, 3) == 1 and L.agca_set_coarse_projection(h, -1) == 1
     assert L.agca_set_coarse_projection(h, 2) == 0 and L.agca_set_coarse_projection(h, 0) == 0
     assert L.agca_set_tile_config(h, 2, 1, 8, 5) == 0
