@@ -1294,6 +1294,8 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
   return AGCA_OK;
 }
 
+}  // extern "C"
+
 namespace {
 // viscosity hierarchy and flags: by the element-wise ratio rule, or (eta_v
 // set) by the gradient rule of Eq. 2.8 on the finest nodal viscosity
@@ -1333,6 +1335,8 @@ agca_status flag_impl(agca_ctx* ctx, double nu, const double* eta_v, size_t* gca
   return AGCA_OK;
 }
 }  // namespace
+
+extern "C" {
 
 agca_status agca_flag(agca_ctx* ctx, double nu, size_t* gca_bytes) { return flag_impl(ctx, nu, nullptr, gca_bytes); }
 
