@@ -1,10 +1,14 @@
-"""Pins of the oracle's coefficient variants: the three P0 projections of the
-coarse coefficient (arithmetic, harmonic, geometric mean, Sec. 3.2 / Fig. 6)
-and the paper's gradient-norm flag rule (Eq. 2.8), each checked against
-closed forms and invariants that do not reuse the oracle's formulas."""
+"""Pins of the oracle's parts for the next rows: the three P0 projections of
+the coarse coefficient (arithmetic, harmonic, geometric mean, Sec. 3.2 /
+Fig. 6), the paper's gradient-norm flag rule (Eq. 2.8) and its outer solver
+(FGMRES with the block-triangular preconditioner of Eq. 4.1 and the
+diag(A)-BFBT of Eq. 4.2), each checked against closed forms and invariants
+that do not reuse the oracle's formulas."""
 import itertools
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 import pytest
 
 from oracle import agca
@@ -114,3 +118,76 @@ def test_gradient_flags_of_a_step():
         want = ccol == (nL // 2 - 1) >> (L - l)
         assert np.array_equal(flags[l], want)
         assert flags[l].sum() == 6 * nl * nl
+
+
+# ---- the paper's outer solver (Sec. 4): FGMRES + block-triangular + BFBT ----
+@pytest.fixture(scope="module")
+def stokes_small():
+    from oracle import stokes as ostokes
+    from synth import sphere_sinkers
+
+    p = sphere_sinkers(2, 2, 0.2, 0.05, 1e3)
+    H = agca.Hierarchy(2, 2, p.eta, 10.0)
+    S = ostokes.Stokes(H)
+    return p, S
+
+
+def test_bfbt_is_exact_for_a_diagonal_velocity_block(stokes_small):
+    """With A replaced by W = diag(A) the Schur complement B W^-1 B^T is Z
+    itself, and Z^-1 (B W^-1 W W^-1 B^T) Z^-1 = Z^-1 (Eq. 4.2)."""
+    from oracle.fgmres import BlockTriangular
+
+    _, S = stokes_small
+    Q = BlockTriangular(S)
+    W = sp.diags(np.where(S.mask > 0, 1.0 / np.where(Q.winv > 0, Q.winv, 1.0), 0.0))
+    Qd = BlockTriangular(S, A_bfbt=W)
+    x = np.random.default_rng(4).normal(size=S.np_)
+    x -= x.mean()
+    assert np.allclose(Qd.bfbt(Qd.Z @ x), x, rtol=0, atol=1e-10 * np.abs(x).max())
+    # the default BFBT differs from Z^-1 (A is not diagonal) but is symmetric
+    y = np.random.default_rng(5).normal(size=S.np_)
+    y -= y.mean()
+    assert abs(Q.bfbt(x) @ y - x @ Q.bfbt(y)) <= 1e-10 * np.linalg.norm(Q.bfbt(x)) * np.linalg.norm(y)
+
+
+def test_exact_block_triangular_fgmres_converges_in_two_steps(stokes_small):
+    """With A~ = A and S~ = S = B A^-1 B^T exact, K Q^-1 = [[I, 0], [B A^-1, I]]
+    has (K Q^-1 - I)^2 = 0, so FGMRES reaches the solution in two steps.  A
+    missing or sign-flipped coupling term A~^-1 B^T S~^-1 takes three (the
+    sign of the Schur block alone is not seen: -S~ and +S~ both give a
+    degree-2 minimal polynomial)."""
+    from oracle.fgmres import BlockTriangular, solve
+
+    p, S = stokes_small
+    iv = np.nonzero(S.mask > 0)[0]
+    lu = spla.splu(S.A[iv][:, iv].tocsc())
+
+    def a_exact(r):
+        z = np.zeros_like(r)
+        z[iv] = lu.solve(r[iv])
+        return z
+
+    Bi = S.B[:, iv].toarray()
+    Sd = Bi @ lu.solve(Bi.T)
+    Spinv = np.linalg.pinv(Sd, rcond=1e-12)
+
+    def s_exact(rp):
+        return Spinv @ (rp - rp.mean())
+
+    b = S.rhs(p.fbar)
+    x, its = solve(S, b, rtol=1e-10, precond=BlockTriangular(S, a_inv=a_exact, s_inv=s_exact))
+    assert its <= 2
+    x_ref = S.direct(b)
+    assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+
+
+def test_fgmres_vcycle_bfbt_matches_direct_solve(stokes_small):
+    from oracle.fgmres import solve
+
+    p, S = stokes_small
+    b = S.rhs(p.fbar)
+    x, its = solve(S, b, rtol=1e-11)
+    x_ref = S.direct(b)
+    assert its > 2
+    assert np.linalg.norm(b - S.K(x)) <= 1.01e-11 * np.linalg.norm(b)
+    assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
