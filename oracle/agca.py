@@ -266,3 +266,45 @@ def flag_hierarchy(N: int, L: int, eta: np.ndarray, nu: float, projection: str =
         mn[l] = mn[l + 1][k].min(axis=1)
         flags[l] = mx[l] > nu * mn[l]
     return mean, mx, mn, flags
+
+
+# Kuhn-grid vertex neighbourhood: the vertex itself and the 14 vertices it
+# shares an element edge with (+-e_i, +-(e_i + e_j), +-(1, 1, 1)); the stencil
+# storage of Remark 5 keeps one 3x3 block per offset
+KUHN_OFFSETS = np.array([(0, 0, 0)] + [s * np.array(d) for d in
+                         [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+                         for s in (1, -1)], dtype=np.int64)
+
+
+def stencil_blocks(H: Hierarchy, l: int) -> np.ndarray:
+    """The level-l operator as per-vertex stencils (Remark 5): out[v, o, c, d]
+    is the coupling of component c at vertex v with component d at vertex
+    v + KUHN_OFFSETS[o] (zero where the neighbour is outside the grid), read
+    from the assembled global matrix."""
+    m = H.mesh[l]
+    n1 = m.n + 1
+    A = H.A[l].tocsr()
+    out = np.zeros((m.nv, len(KUHN_OFFSETS), 3, 3))
+    for o, d in enumerate(KUHN_OFFSETS):
+        nb = m.ijk + d
+        ok = ((nb >= 0) & (nb <= m.n)).all(axis=1)
+        v = np.nonzero(ok)[0]
+        w = nb[ok, 0] + n1 * (nb[ok, 1] + n1 * nb[ok, 2])
+        for c in range(3):
+            for e in range(3):
+                out[v, o, c, e] = np.asarray(A[c * m.nv + v, e * m.nv + w]).ravel()
+    return out
+
+
+def stencil_apply(H: Hierarchy, l: int, blocks: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A_l x from the per-vertex stencils of stencil_blocks."""
+    m = H.mesh[l]
+    n1 = m.n + 1
+    X = x.reshape(3, m.nv).T
+    Y = np.zeros((m.nv, 3))
+    for o, d in enumerate(KUHN_OFFSETS):
+        nb = m.ijk + d
+        ok = ((nb >= 0) & (nb <= m.n)).all(axis=1)
+        w = np.where(ok, nb[:, 0] + n1 * (nb[:, 1] + n1 * nb[:, 2]), 0)
+        Y += np.einsum("vce,ve->vc", blocks[:, o], X[w] * ok[:, None])
+    return Y.T.ravel()

@@ -191,3 +191,24 @@ def test_fgmres_vcycle_bfbt_matches_direct_solve(stokes_small):
     assert its > 2
     assert np.linalg.norm(b - S.K(x)) <= 1.01e-11 * np.linalg.norm(b)
     assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+
+
+# ---- stencil storage of the coarse operators (Remark 5) ----
+def test_agca_rows_fit_the_15_point_kuhn_stencil():
+    """Every level's AGCA operator, with DCA and stored Galerkin elements
+    mixed, couples a vertex only with itself and its 14 Kuhn neighbours, so
+    per-vertex 15-offset stencils hold it exactly: the stencils rebuild the
+    matrix (nonzero count included) and apply as the matrix does."""
+    from synth import sphere_sinkers
+
+    p = sphere_sinkers(4, 3, 0.15, 0.02, 1e4)
+    H = agca.Hierarchy(4, 3, p.eta, 10.0)
+    assert sum(len(H.flist[l]) for l in (1, 2)) > 0
+    for l in (1, 2, 3):
+        blocks = agca.stencil_blocks(H, l)
+        nnz_stencil = np.count_nonzero(blocks)
+        assert nnz_stencil == H.A[l].count_nonzero(), l  # nothing outside the 15 offsets
+        x = np.random.default_rng(l).normal(size=3 * H.mesh[l].nv)
+        y = agca.stencil_apply(H, l, blocks, x)
+        assert np.allclose(y, H.A[l] @ x, rtol=0, atol=1e-12 * np.abs(H.A[l] @ x).max()), l
+    assert len(agca.KUHN_OFFSETS) == 15 and len({tuple(o) for o in agca.KUHN_OFFSETS}) == 15
