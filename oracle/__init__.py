@@ -11,7 +11,8 @@ Modules:
   mesh      Kuhn meshes, geometry, parent/child maps, interpolation (Sec. 2, Eq. 2.2, Eq. 2.4)
   fem       element matrices and global assembly of Eqs. 3.4-3.5
   agca      viscosity hierarchy (arithmetic / harmonic / geometric coarse means), flags (ratio
-            rule; gradient rule of Eq. 2.8), element-wise Galerkin (Eqs. 2.6-2.9), V-cycle
+            rule; gradient rule of Eq. 2.8), element-wise Galerkin (Eqs. 2.6-2.9), V-cycle,
+            per-vertex 15-offset stencils of the level operators (Remark 5)
   stokes    Stokes operator, MINRES (Remark 6), direct solve, adjoint gradient
   fgmres    the paper's outer solver: FGMRES, block-triangular Q (Eq. 4.1), diag(A)-BFBT (Eq. 4.2)
   pointwise per-vertex rows of the fine operator for sampled checks at large sizes
