@@ -208,8 +208,13 @@ agca_status agca_adjoint_gradient(agca_ctx* ctx, const double* x_dev, const doub
  *   eta: double[6 (2N)^3] element viscosities (as agca_set_viscosity);
  *   x, y: double[3 (2N+1)^3 + (N+1)^3] Stokes vectors as agca_stokes_apply;
  *   cuda_stream: cudaStream_t (NULL = legacy default stream).
- * The first call on a device looks up the scratch address on that device
- * (make it before any stream capture).  Every call uses the same scratch and
+ * eta, x and y must be device memory of the current device (AGCA_EINVAL
+ * otherwise); the stream must belong to the current device.
+ * The scratch array's device address belongs to a CUDA context: the first
+ * call under each context (normally once per device, in its primary
+ * context) looks it up and caches it by the context's unique ID, so a call
+ * under another context never uses a stale address.  Make that first call
+ * before any stream capture.  Every call uses the same scratch and
  * overwrites all of it that it reads, so nothing needs clearing; calls that
  * overlap on the GPU (other streams, other host threads) race on it.
  * Asynchronous; returns AGCA_ECUDA if a launch fails. */

@@ -24,14 +24,19 @@ class StokesProblem:
         self.ctx = Context(N, levels, precision, device=device)
         self.fbar = fbar
         self.nu, self.rtol, self.maxit = nu, rtol, maxit
-        self._theta_version = None
+        self._theta_prepared = None  # copy of the theta the hierarchy was built for
         self.last_iters = (0, 0)
 
     def _prepare(self, theta: torch.Tensor):
-        key = (theta.data_ptr(), theta._version, float(theta.sum()))
-        if key != self._theta_version:
-            self.ctx.prepare(torch.exp(theta.detach()).contiguous(), self.nu)
-            self._theta_version = key
+        # the hierarchy (flags, Galerkin matrices) is rebuilt unless it was
+        # built for exactly these values: an element-wise comparison on the
+        # device, so two different fields can never share a hierarchy
+        t = theta.detach()
+        if self._theta_prepared is not None and self._theta_prepared.shape == t.shape and \
+                torch.equal(self._theta_prepared, t):
+            return
+        self.ctx.prepare(torch.exp(t).contiguous(), self.nu)
+        self._theta_prepared = t.clone()
 
     def solve(self, theta: torch.Tensor) -> torch.Tensor:
         self._prepare(theta)

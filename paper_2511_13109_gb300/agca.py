@@ -145,8 +145,13 @@ def stokes_apply_static(N: int, eta: torch.Tensor, x: torch.Tensor, y: torch.Ten
     _need(x, nt, torch.float64, "x")
     y = torch.empty_like(x) if y is None else y
     _need(y, nt, torch.float64, "y")
+    if not (eta.device == x.device == y.device):
+        raise ValueError(f"eta, x and y must be on one device (got {eta.device}, {x.device}, {y.device})")
     s = stream if stream is not None else torch.cuda.current_stream(x.device)
-    st = lib().agca_stokes_apply_static(N, _ptr(eta), _ptr(x), _ptr(y), _P(s.cuda_stream))
+    if s.device != x.device:
+        raise ValueError(f"the stream is on {s.device}, the tensors on {x.device}")
+    with torch.cuda.device(x.device):  # the library works on the current device
+        st = lib().agca_stokes_apply_static(N, _ptr(eta), _ptr(x), _ptr(y), _P(s.cuda_stream))
     if st != 0:
         raise AgcaError(st, f"agca_stokes_apply_static(N={N})")
     return y

@@ -48,9 +48,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     exe = nvcc()
     procs = []
     objs = []
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "agca.h")]
+    t_hdr = max(os.path.getmtime(p) for p in headers)
     for src in sources():
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
+        # an object is reused while it is newer than its source and every header
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), t_hdr):
+            continue
         cmd = [exe, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

@@ -20,7 +20,6 @@ DR^-0.5``, ``eta_high = DR^0.5``, forcing ``f = (0, 0, -xi)``.
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import numpy as np
 import torch
@@ -257,8 +256,3 @@ def adjoint_problem(N: int, seed: int = CONFIG_SEED0 + 4, device="cpu"):
 def random_vector(size: int, seed: int) -> np.ndarray:
     """Uniform [-1, 1] float64 test vector."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=size)
-
-
-def _self_check():  # pragma: no cover - debugging aid
-    p = cube_sinker(2)
-    print(p.eta.shape, math.isfinite(p.eta.sum()))
