@@ -1,12 +1,19 @@
 """Benchmark: fine-level velocity DoF/s per AGCA V-cycle and Stokes solve time
-to a 1e-8 relative residual, on synthetic 8-sphere sinker problems.
+to a 1e-8 relative residual, on synthetic sinker problems.
 
-Workload (default): 64^3 pressure cubes (128^3 velocity cubes, 6,440,067
-velocity DoF, 6 levels), 8 tanh-smoothed spherical sinkers with seeded
-centres in [0.2, 0.8]^3, radius 0.08, width 0.01, jump 1e6, threshold nu = 10.
-A step is one V(2,2) cycle of the mixed-precision preconditioner (FP32 cycle)
-on a residual resident in HBM; the whole-solve times (setup and MINRES to
-1e-8, FP64 and mixed) are reported beside it.
+Workload (default): the mixed-precision-at-scale configuration: 128^3
+pressure cubes (256^3 velocity cubes, 50,923,779 velocity DoF, 2,146,689
+pressure DoF, 7 levels), log10 viscosity = sum of 20 seeded Gaussian bumps
+(amplitudes in [-3, 3], widths in [0.03, 0.15]) clipped to [-3, 3], forcing
+f_z = -(log10 mu + 3)/6, AGCA threshold nu = 10.
+
+A step is one V(2,2) cycle of the FP64 AGCA preconditioner on a residual
+resident in HBM (`value`, dtype f64: the paper's precision).  Beside it, on
+the same field: the mixed-precision cycle (FP32 smoothing, transfers and
+coarse applies), setup + MINRES time to 1e-8 for the FP64 and mixed solvers,
+AGCA (nu = 10) against pure DCA (no flagged element) on the 8-sphere 64^3
+field with jump 1e6, the 24-problem batch (uneven 32^3/48^3/64^3 single
+sinkers, batched against one by one), and the CPU oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,10 +41,18 @@ import torch  # noqa: E402
 
 METRIC = "fine-level velocity DoF/s per V-cycle; Stokes solve time to 1e-8 rel. residual"
 UNIT = "DoF/s"
+NU = 10.0
+NU_DCA = 1e300  # no element's max/min viscosity ratio reaches it: pure DCA on every coarse level
 
+# FP64 arithmetic peak from the unit counts and clock: 152 SMs x 2 FP64
+# fused multiply-adds per SM and clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-def workload_params(N):
-    return dict(N=N, n_sinkers=8, radius=0.08, width=0.01, dr=1e6, nu=10.0)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per finest-level
+# stencil launch, mean over the four launches of one V-cycle, from one ncu
+# capture of the current kernels (None where no capture of the current
+# kernel exists)
+FINE_STENCIL_DRAM_BYTES = {("logbump", 128, "f64"): None, ("logbump", 128, "f32"): None}
 
 
 def _dist():
@@ -82,7 +97,7 @@ class ClockSampler:
         self.first = ""
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             # nvidia-smi's start-up (NVML initialisation) must not overlap the timed region
             self.first = self.proc.stdout.readline()
@@ -123,15 +138,6 @@ def _peaks():
         return {}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per finest-level
-# stencil launch of the 64^3 workload, mean over the four launches of one
-# V-cycle (pre-smoothing 109.8 MB, residual 106.0 MB, first post-smoothing step
-# 135.0 MB, last step with the FP64-widened result 183.2 MB), from one ncu
-# capture of the current kernel; the algorithmic bytes of the same launches
-# average 154.6 MB (part of the inputs is still in L2 from the previous launch)
-FINE_STENCIL_DRAM_BYTES = 133.5e6
-
-
 def bench_levels(N):
     """Levels of the benchmark hierarchy: coarsen the 2N velocity grid while
     it stays even with >= 4 cubes (the library's default)."""
@@ -142,24 +148,56 @@ def bench_levels(N):
     return L
 
 
-def arm_config(N, L, flagged, world):
-    return {"workload": "8-sphere sinker, jump 1e6, nu 10, V(2,2) mixed AGCA cycle",
+def workload_name(field, N, L):
+    if field == "logbump":
+        return (f"20 Gaussian log10-viscosity bumps clipped to [1e-3, 1e3], {N}^3 pressure cubes "
+                f"({3 * (2 * N + 1) ** 3:,} velocity DoF, {L} levels), AGCA nu 10, V(2,2) cycle")
+    return (f"8 tanh spheres r 0.08 w 0.01 jump 1e6, {N}^3 pressure cubes "
+            f"({3 * (2 * N + 1) ** 3:,} velocity DoF, {L} levels), AGCA nu 10, V(2,2) cycle")
+
+
+def arm_config(field, N, L, flagged, world):
+    return {"workload": workload_name(field, N, L), "field": field,
             "N_pressure": N, "velocity_cubes": 2 * N, "levels": L, "velocity_dofs": 3 * (2 * N + 1) ** 3,
-            "flagged_per_level": flagged, "global_batch": world, "seq_len": None,
+            "pressure_dofs": (N + 1) ** 3, "flagged_per_level": flagged, "global_batch": world, "seq_len": None,
             "parallelism": f"replicas{world}",
-            "l2": "inputs larger than L2 (cycle working set ~0.3 GB > 129 MB), no flush"}
+            "l2": "inputs larger than L2 (one FP64 velocity vector is "
+                  f"{3 * (2 * N + 1) ** 3 * 8 / 1e6:.0f} MB > 129 MB), no flush"}
 
 
-def oracle_vcycle_rate(seconds=15.0, N=16):
-    """CPU oracle: DoF/s of its V-cycle on the same field family at a size it
-    handles in seconds (the 64^3 hierarchy does not fit its sparse matrices)."""
+def make_field(field, N, dev):
+    """(eta (E,), fbar (3E,)) on the device."""
+    if field == "logbump":
+        from synth import gaussian_logbumps_on_device
+
+        eta, fbar = gaussian_logbumps_on_device(N, device=dev)
+    else:
+        from synth import sphere_sinkers_on_device
+
+        eta, fbar, _ = sphere_sinkers_on_device(N, 8, 0.08, 0.01, 1e6, device=dev)
+    return eta, fbar.reshape(-1)
+
+
+def host_field(field, N):
+    from synth import gaussian_logbumps, sphere_sinkers
+
+    return gaussian_logbumps(N) if field == "logbump" else sphere_sinkers(N, 8, 0.08, 0.01, 1e6)
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_timings(field, seconds=10.0, N=16, solve=True):
+    """The oracle as it stands, on the host cores: DoF/s of its V-cycle on the
+    workload's field family at a size it handles in seconds, and its MINRES
+    solve to 1e-8 at the same size.  scipy's CSR products run on one thread."""
     from oracle import agca as oagca
-    from synth import random_vector, sphere_sinkers
+    from oracle import stokes as ostokes
+    from synth import random_vector
 
-    prm = workload_params(N)
-    p = sphere_sinkers(N, prm["n_sinkers"], prm["radius"], prm["width"], prm["dr"])
-    L = {8: 3, 16: 4, 32: 5}.get(N, 4)
-    H = oagca.Hierarchy(N, L, p.eta, prm["nu"])
+    p = host_field(field, N)
+    L = bench_levels(N)
+    t0 = time.perf_counter()
+    H = oagca.Hierarchy(N, L, p.eta, NU)
+    setup_s = time.perf_counter() - t0
     n = 3 * H.mesh[L].nv
     r = random_vector(n, 3) * H.mask[L]
     H.vcycle(r)
@@ -169,61 +207,203 @@ def oracle_vcycle_rate(seconds=15.0, N=16):
         H.vcycle(r)
         k += 1
     dt = (time.perf_counter() - t0) / k
-    dofs = 3 * (2 * N + 1) ** 3
-    # the V-cycle's work is scipy CSR products, which run on one thread
-    return dofs / dt, k, dt, 1
+    out = {"N": N, "levels": L, "vcycles": k, "vcycle_ms": dt * 1e3, "vcycle_dofs_per_s": n / dt,
+           "setup_s": setup_s}
+    if solve:
+        S = ostokes.Stokes(H)
+        b = S.rhs(p.fbar)
+        t0 = time.perf_counter()
+        x, its = S.minres(b, 1e-8, 20000)
+        out["solve_s"] = time.perf_counter() - t0
+        out["minres_iters"] = its
+        out["relres"] = float(np.linalg.norm(b - S.K(x)) / np.linalg.norm(b))
+    return out
+
+
+def _cores():
+    try:
+        import threadpoolctl
+
+        info = threadpoolctl.threadpool_info()
+        blas = max((i.get("num_threads", 1) for i in info), default=1)
+    except Exception:  # noqa: BLE001
+        blas = None
+    return os.cpu_count(), blas
 
 
 def run_reference(args):
-    """The oracle as it stands, timed on the host cores: each step is one
-    oracle V-cycle of the benchmark's field family at 16^3 pressure cubes (a
-    bounded sample of the 64^3 workload, whose hierarchy the oracle's sparse
-    matrices do not fit in seconds), reported as DoF/s on the same config."""
+    """--impl reference: the oracle as it stands, timed on the host cores.
+    Each step is one oracle V-cycle of the workload's field family at 16^3
+    pressure cubes (a bounded sample: the oracle's sparse matrices of the
+    128^3 hierarchy take tens of GB and minutes per cycle); the config names
+    the size actually timed."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     from oracle import agca as oagca
-    from synth import random_vector, sphere_sinkers
-
-    Nw = args.N or 64
-    Lw = bench_levels(Nw)
-    pw = workload_params(Nw)
-    pfull = sphere_sinkers(Nw, pw["n_sinkers"], pw["radius"], pw["width"], pw["dr"])
-    _, _, _, flags = oagca.flag_hierarchy(Nw, Lw, pfull.eta, pw["nu"])
-    flagged = [int(flags[l].sum()) for l in range(1, Lw)]
-    del pfull
+    from synth import random_vector
 
     N = 16
-    prm = workload_params(N)
-    p = sphere_sinkers(N, prm["n_sinkers"], prm["radius"], prm["width"], prm["dr"])
-    H = oagca.Hierarchy(N, 4, p.eta, prm["nu"])
-    n = 3 * H.mesh[4].nv
-    r = random_vector(n, 3) * H.mask[4]
+    L = bench_levels(N)
+    p = host_field(args.field, N)
+    H = oagca.Hierarchy(N, L, p.eta, NU)
+    n = 3 * H.mesh[L].nv
+    r = random_vector(n, 3) * H.mask[L]
     for _ in range(args.warmup):
         H.vcycle(r)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         H.vcycle(r)
     dt = (time.perf_counter() - t0) / args.steps
-    dofs = 3 * (2 * N + 1) ** 3
-    value = dofs / dt
+    value = n / dt
+    ncpu, blas = _cores()
+    cfg = arm_config(args.field, N, L, [int(H.flags[l].sum()) for l in range(1, L)], 1)
+    cfg["sample_of"] = workload_name(args.field, args.N, bench_levels(args.N))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": arm_config(Nw, Lw, flagged, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} oracle V-cycles at 16^3 pressure cubes of the same "
-                                       f"8-sphere field family ({dt * 1e3:.0f} ms each; scipy CSR products "
-                                       f"on one thread)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cpu_count": ncpu,
+                             "blas_threads": blas, "kind": "oracle",
+                             "sample": f"{args.steps} oracle V-cycles at {N}^3 pressure cubes of the same field "
+                                       f"family ({dt * 1e3:.0f} ms each; scipy CSR products on one thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# ------------------------------------------------------------------ GPU parts
+def time_cycles(ctx, r, z, steps, stream, nvtx=None):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.vcycle(r, z)
+    e1.record(stream)
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def fine_profile(ctx, r, z, reps):
+    """Per-launch CUDA-event times of the finest-level stencil launches over
+    reps cycles: (mean ms per launch, algorithmic bytes and flops per launch)."""
+    ctx.profile_fine(True)
+    for _ in range(reps):
+        ctx.vcycle(r, z)
+    ms, by, fl, n = ctx.profile_fine(False)
+    return ms / n, by / n, fl / n, n
+
+
+def e2e_rate(ctx, r, dofs, steps, stream, dev):
+    """The same cycle through the API with host buffers: every step copies its
+    residual in from pinned host memory and its result back out.  Steps are
+    pipelined: two device buffer pairs, one copy stream per direction, so
+    step i's copies overlap the cycles of steps i -+ 1."""
+    r_h = r.cpu().pin_memory()
+    z_h = torch.empty_like(r_h).pin_memory()
+    r_d = [torch.empty_like(r) for _ in range(2)]
+    z_d = [torch.empty_like(r) for _ in range(2)]
+    h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: [torch.cuda.Event() for _ in range(2)]  # noqa: E731
+    in_ready, cycle_done, out_done = ev(), ev(), ev()
+
+    def run(k):
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        h2d.wait_event(start)
+        for i in range(k):
+            j = i % 2
+            if i >= 2:
+                h2d.wait_event(cycle_done[j])  # r_d[j] consumed by step i-2
+            with torch.cuda.stream(h2d):
+                r_d[j].copy_(r_h, non_blocking=True)
+            in_ready[j].record(h2d)
+            stream.wait_event(in_ready[j])
+            if i >= 2:
+                stream.wait_event(out_done[j])  # z_d[j] read back by step i-2
+            ctx.vcycle(r_d[j], z_d[j])
+            cycle_done[j].record(stream)
+            d2h.wait_event(cycle_done[j])
+            with torch.cuda.stream(d2h):
+                z_h.copy_(z_d[j], non_blocking=True)
+            out_done[j].record(d2h)
+        stream.wait_event(out_done[(k - 1) % 2])
+        end = torch.cuda.Event(enable_timing=True)
+        end.record(stream)
+        end.synchronize()
+        return start.elapsed_time(end)
+
+    run(3)
+    ms = run(steps) / steps
+    return dofs / (ms * 1e-3), ms, int(r.numel() * 8)
+
+
+def timed_solve(pkg, N, L, prec, eta, fbar, nu, dev, stream, maxit, tune_cache=None):
+    """Setup (flags, Galerkin, diagonals, lambda, coarsest factor) + MINRES to
+    1e-8 from x = 0, wall clock with the device synchronised on both sides."""
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    c = pkg.Context(N, L, prec, device=dev, stream=stream)
+    c.prepare(eta, nu)
+    if tune_cache is not None:
+        c.autotune(10, tune_cache)  # tile shapes read back from the cycle's tuning run
+    b = c.load_vector(fbar)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    try:
+        x, its, rel = c.solve(b, 1e-8, maxit)
+        conv = True
+    except pkg.AgcaError as e:  # stopped at the iteration limit above the tolerance
+        if e.status != 4:
+            raise
+        x, its, rel, conv = None, maxit, float("nan"), False
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    nflag = [c.level_info(l).n_flag for l in range(1, L)]
+    del c
+    return {"time_to_1e-8_s": t2 - t0, "setup_s": t1 - t0, "solve_s": t2 - t1, "minres_iters": its,
+            "relres": rel, "converged": conv, "flagged_per_level": nflag}, x
+
+
+def solves(pkg, N, L, eta, fbar, dev, stream, tune64, tune32, reps_mixed=3):
+    out = {}
+    res, x64 = timed_solve(pkg, N, L, pkg.FP64, eta, fbar, NU, dev, stream, 20000, tune64)
+    out["fp64"] = res
+    runs = []
+    xm = None
+    for _ in range(reps_mixed):
+        res, xm = timed_solve(pkg, N, L, pkg.MIXED, eta, fbar, NU, dev, stream, 20000, tune32)
+        runs.append(res)
+    runs.sort(key=lambda d: d["time_to_1e-8_s"])
+    out["mixed"] = dict(runs[len(runs) // 2], repetitions=reps_mixed)
+    out["fp64"]["repetitions"] = 1
+    if x64 is not None and xm is not None:
+        # both solutions reach the 1e-8 residual: their difference bounds the
+        # mixed solution's error against the FP64 one at that tolerance
+        out["mixed_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
+    return out
+
+
+def agca_vs_dca(pkg, dev, stream):
+    """AGCA (nu = 10) against pure DCA on the 8-sphere 64^3 field with jump
+    1e6 (Sec. 4.2: DCA loses robustness at unaligned jumps): mixed solves to
+    1e-8, iterations and time, same field and forcing."""
+    N = 64
+    L = bench_levels(N)
+    eta, fbar = make_field("spheres", N, dev)
+    out = {"workload": workload_name("spheres", N, L) + ", mixed solve to 1e-8"}
+    for name, nu, maxit in (("agca_nu10", NU, 20000), ("dca", NU_DCA, 20000)):
+        res, _ = timed_solve(pkg, N, L, pkg.MIXED, eta, fbar, nu, dev, stream, maxit)
+        out[name] = res
+    return out
+
+
 def run_batch(args, dev, stream):
-    """The 24-problem batch (uneven 32^3/48^3/64^3 sinkers): batched V-cycle
-    throughput against the same problems cycled one by one, and batched solve
-    time to 1e-8 against sequential solves."""
+    """The 24-problem batch (uneven 32^3/48^3/64^3 single sinkers): batched
+    V-cycle throughput against the same problems cycled one by one, and
+    batched solve time to 1e-8 against sequential solves."""
     import paper_2511_13109_gb300 as pkg
     from synth import batch_problems
 
@@ -236,7 +416,7 @@ def run_batch(args, dev, stream):
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         b = pkg.Batch([p.N for p in probs], pkg.MIXED, device=dev, stream=stream)
-        b.prepare(etas, 10.0)
+        b.prepare(etas, NU)
         stream.synchronize()
         out["setup_s"] = time.perf_counter() - t0
         rs = [torch.rand(3 * c.V[c.L], dtype=torch.float64, device=dev) * 2 - 1 for c in b.contexts]
@@ -255,7 +435,7 @@ def run_batch(args, dev, stream):
         singles = []
         for p, eta in zip(probs, etas):
             c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.MIXED, device=dev, stream=stream)
-            c.prepare(eta, 10.0)
+            c.prepare(eta, NU)
             singles.append(c)
         for c, r, z in zip(singles, rs, zs):
             c.vcycle(r, z)
@@ -279,25 +459,37 @@ def run_batch(args, dev, stream):
             for c, bb in zip(singles, bs):
                 c.solve(bb, 1e-8, 40000)
             stream.synchronize()
-            out["sequential_solve_s"] = time.perf_counter() - t0
+            out["sequential_mixed_solve_s"] = time.perf_counter() - t0
+            # the plain FP64 form of the same problems, one by one
+            t0 = time.perf_counter()
+            for p, eta, bb in zip(probs, etas, bs):
+                c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.FP64, device=dev, stream=stream)
+                c.prepare(eta, NU)
+                c.solve(bb, 1e-8, 40000)
+                del c
+            stream.synchronize()
+            out["sequential_fp64_solve_s"] = time.perf_counter() - t0
+        del singles, b
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--field", default="logbump", choices=["logbump", "spheres"])
+    ap.add_argument("--mixed-steps", type=int, default=200, help="timed mixed-precision cycles")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--batch", action="store_true", help="also run the 24-problem batch")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-dca", action="store_true")
     ap.add_argument("--batch-n", type=int, default=0)
-    ap.add_argument("--solve-iters", type=int, default=0,
-                    help="profiling aid: run only K MINRES iterations of the workload's mixed solve "
-                         "inside the NVTX range 'solve', print one short JSON line and exit")
+    ap.add_argument("--cycles-only", action="store_true",
+                    help="profiling aid: warm-up and timed cycles of both precisions only, one short JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -311,43 +503,26 @@ def main():
 
     __graft_entry__.build()
     import paper_2511_13109_gb300 as pkg
-    from synth import sphere_sinkers_on_device
 
-    prm = workload_params(args.N)
-    N = prm["N"]
+    N = args.N
     L = pkg.default_levels(N)
-    # element fields generated on the device (no host copies: 26 GB at N = 256)
-    eta, fbar, _ = sphere_sinkers_on_device(N, prm["n_sinkers"], prm["radius"], prm["width"], prm["dr"], device=dev)
-    fbar = fbar.reshape(-1)
-
+    eta, fbar = make_field(args.field, N, dev)
     stream = torch.cuda.Stream(device=dev)
+    tune_dir = tempfile.mkdtemp(prefix="agca_bench_")
     with torch.cuda.stream(stream):
-        ctx = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
-        ctx.prepare(eta, prm["nu"])
-        if args.no_solve and args.solve_iters <= 0:
-            fbar = None  # only the solves load it
+        ctx = pkg.Context(N, L, pkg.FP64, device=dev, stream=stream)
+        ctx.prepare(eta, NU)
         t_tune = time.perf_counter()
-        tune_cache = os.path.join(tempfile.mkdtemp(prefix="agca_bench_"), "tiles.txt")
-        tuned = ctx.autotune(reps=10, cache=tune_cache) if not args.no_tune else {}
+        tune64 = os.path.join(tune_dir, "tiles64.txt")
+        tuned = ctx.autotune(reps=5, cache=tune64) if not args.no_tune else {}
         t_tune = time.perf_counter() - t_tune
-        if args.solve_iters > 0:
-            b = ctx.load_vector(fbar)
-            stream.synchronize()
-            torch.cuda.nvtx.range_push("solve")
-            try:
-                _, its, rel = ctx.solve(b, 1e-8, args.solve_iters)
-            except pkg.AgcaError as e:  # stopped at the iteration limit above the tolerance
-                its, rel = args.solve_iters, str(e)
-            stream.synchronize()
-            torch.cuda.nvtx.range_pop()
-            if rank == 0:
-                print(json.dumps({"solve_iters": its, "relres": rel}), flush=True)
-            return 0
-        n3 = 3 * ctx.V[L]
+        dofs = 3 * ctx.V[L]
         g = torch.Generator(device=dev)
         g.manual_seed(1234 + rank)
-        r = torch.rand(n3, dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        r = torch.rand(dofs, dtype=torch.float64, device=dev, generator=g) * 2 - 1
         z = torch.empty_like(r)
+
+        # ---- the timed region: K FP64 V(2,2) cycles
         for _ in range(args.warmup):
             ctx.vcycle(r, z)
         stream.synchronize()
@@ -370,129 +545,90 @@ def main():
         _barrier(dist)
         ms_total = _max_over_ranks(dist, ms_total, dev)
         ms_step = ms_total / args.steps
-        dofs = 3 * ctx.V[L]
         value = dofs * world / (ms_step * 1e-3)
 
-        # per-launch timing of the dominant (finest-level stencil) kernels
-        ctx.profile_fine(True)
-        for _ in range(min(args.steps, 500)):
-            ctx.vcycle(r, z)
-        k_ms, k_bytes, k_launches = ctx.profile_fine(False)
-        achieved = k_bytes / (k_ms * 1e-3) / 1e9
+        # ---- the mixed-precision cycle on the same field
+        ctxm = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
+        ctxm.prepare(eta, NU)
+        tune32 = os.path.join(tune_dir, "tiles32.txt")
+        tunedm = ctxm.autotune(reps=10, cache=tune32) if not args.no_tune else {}
+        for _ in range(max(3, args.warmup)):
+            ctxm.vcycle(r, z)
+        mixed_ms = time_cycles(ctxm, r, z, args.mixed_steps, stream, nvtx="mixed")
+        if args.cycles_only:
+            if rank == 0:
+                print(json.dumps({"fp64_ms": ms_step, "mixed_ms": mixed_ms}), flush=True)
+            return 0
+
+        # ---- dominant kernels: per-launch CUDA-event times of the finest stencils
+        k64_ms, k64_bytes, k64_flops, k64_n = fine_profile(ctx, r, z, min(max(args.steps, 5), 50))
+        k32_ms, k32_bytes, _, k32_n = fine_profile(ctxm, r, z, 200)
         peaks = _peaks()
-        peak = peaks.get("hbm_gbs", 6800.0)
+        hbm_peak = peaks.get("hbm_gbs")
+        hbm_src = "measured hbm_gbs (MEASURED_PEAKS.json)" if hbm_peak else "fallback 6800 GB/s"
+        hbm_peak = hbm_peak or 6800.0
 
-        # end to end through the API with host buffers: every step copies its
-        # residual in from pinned host memory and its result back out.  Steps
-        # are pipelined: two device buffer pairs, one copy stream per
-        # direction, so step i's copies overlap the cycles of steps i -+ 1
-        r_h = r.cpu().pin_memory()
-        z_h = torch.empty_like(r_h).pin_memory()
-        r_d = [torch.empty_like(r) for _ in range(2)]
-        z_d = [torch.empty_like(r) for _ in range(2)]
-        h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        ev = lambda: [torch.cuda.Event() for _ in range(2)]
-        in_ready, cycle_done, out_done = ev(), ev(), ev()
-
-        def e2e_steps(k):
-            start = torch.cuda.Event(enable_timing=True)
-            start.record(stream)
-            h2d.wait_event(start)
-            for i in range(k):
-                j = i % 2
-                if i >= 2:
-                    h2d.wait_event(cycle_done[j])  # r_d[j] consumed by step i-2
-                with torch.cuda.stream(h2d):
-                    r_d[j].copy_(r_h, non_blocking=True)
-                in_ready[j].record(h2d)
-                stream.wait_event(in_ready[j])
-                if i >= 2:
-                    stream.wait_event(out_done[j])  # z_d[j] read back by step i-2
-                ctx.vcycle(r_d[j], z_d[j])
-                cycle_done[j].record(stream)
-                d2h.wait_event(cycle_done[j])
-                with torch.cuda.stream(d2h):
-                    z_h.copy_(z_d[j], non_blocking=True)
-                out_done[j].record(d2h)
-            stream.wait_event(out_done[(k - 1) % 2])
-            end = torch.cuda.Event(enable_timing=True)
-            end.record(stream)
-            end.synchronize()
-            return start.elapsed_time(end)
-
-        e_steps = max(10, min(args.steps, 200))
-        e2e_steps(4)
-        e2e_ms = _max_over_ranks(dist, e2e_steps(e_steps) / e_steps, dev)
-        e2e_value = dofs * world / (e2e_ms * 1e-3)
-
-        # FP64 cycle beside it
-        ctx64 = pkg.Context(N, L, pkg.FP64, device=dev, stream=stream)
-        ctx64.prepare(eta, prm["nu"])
-        for _ in range(3):
-            ctx64.vcycle(r, z)
-        k64 = max(5, min(args.steps // 20, 100))
-        e0.record(stream)
-        for _ in range(k64):
-            ctx64.vcycle(r, z)
-        e1.record(stream)
-        e1.synchronize()
-        fp64_ms = e0.elapsed_time(e1) / k64
+        # ---- end to end through the API with host buffers
+        e_steps = max(5, min(args.steps, 50))
+        e2e_value, e2e_ms, nbytes = e2e_rate(ctx, r, dofs, e_steps, stream, dev)
+        e2e_value = dofs * world / (_max_over_ranks(dist, e2e_ms, dev) * 1e-3)
 
         solve = None
         if not args.no_solve:
-            solve = {}
-            for name, prec in (("mixed", pkg.MIXED), ("fp64", pkg.FP64)):
-                times = []
-                for rep in range(3):
-                    torch.cuda.synchronize(dev)
-                    t0 = time.perf_counter()
-                    c = pkg.Context(N, L, prec, device=dev, stream=stream)
-                    c.prepare(eta, prm["nu"])
-                    if prec == pkg.MIXED and not args.no_tune:
-                        c.autotune(10, tune_cache)  # tile shapes read back from the cycle's tuning run
-                    b = c.load_vector(fbar)
-                    torch.cuda.synchronize(dev)
-                    t1 = time.perf_counter()
-                    x, its, rel = c.solve(b, 1e-8, 20000)
-                    torch.cuda.synchronize(dev)
-                    t2 = time.perf_counter()
-                    times.append((t2 - t0, t1 - t0, t2 - t1, its, rel))
-                    del c
-                times.sort()
-                tot, st, sv, its, rel = times[len(times) // 2]
-                solve[name] = {"time_to_1e-8_s": tot, "setup_s": st, "solve_s": sv, "minres_iters": its,
-                               "relres": rel}
+            solve = solves(pkg, N, L, eta, fbar, dev, stream, None if args.no_tune else tune64,
+                           None if args.no_tune else tune32)
+        flagged = [ctx.level_info(l).n_flag for l in range(1, L)]
+        del ctxm
 
-    batch = run_batch(args, dev, stream) if args.batch else None
+    dca = None
+    if not args.no_solve and not args.no_dca:
+        dca = agca_vs_dca(pkg, dev, stream)
+    batch = run_batch(args, dev, stream) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, k, dt, cores = oracle_vcycle_rate(12.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{k} oracle V-cycles at 16^3 pressure cubes of the same 8-sphere field family "
-                         f"({dt * 1e3:.0f} ms each; scipy CSR products on one thread)"}
+        o = oracle_timings(args.field, 10.0, 16, solve=not args.no_solve)
+        ncpu, blas = _cores()
+        cpu = {"value": o["vcycle_dofs_per_s"], "unit": UNIT, "cores": 1, "host_cpu_count": ncpu,
+               "blas_threads": blas, "kind": "oracle",
+               "sample": f"{o['vcycles']} oracle V-cycles at 16^3 pressure cubes of the same field family "
+                         f"({o['vcycle_ms']:.0f} ms each; scipy CSR products on one thread)",
+               "oracle_16cubed": o}
 
     if rank == 0:
-        flagged = [ctx.level_info(l).n_flag for l in range(1, L)]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": arm_config(N, L, flagged, world),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": FINE_STENCIL_DRAM_BYTES if N == 64 else None,
-                         "traffic_unit": "DRAM bytes per finest-level stencil launch (ncu)",
-                         "kernel": "finest-level stencil (Chebyshev/residual epilogues), FP32",
-                         "launches_timed": k_launches, "peak_source": "measured hbm_gbs"},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": arm_config(args.field, N, L, flagged, world),
+            "roofline": {"bound": "alu", "achieved": k64_flops / (k64_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": k64_flops / (k64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "traffic": FINE_STENCIL_DRAM_BYTES.get((args.field, N, "f64")),
+                         "kernel": "finest-level FP64 stencil (Chebyshev/residual epilogues)",
+                         "launch_ms": k64_ms, "algorithmic_flops_per_launch": k64_flops,
+                         "algorithmic_bytes_per_launch": k64_bytes,
+                         "hbm_frac_of_measured": k64_bytes / (k64_ms * 1e-3) / 1e9 / hbm_peak,
+                         "launches_timed": k64_n,
+                         "peak_source": "FP64 FMA rate from unit counts and clock (152 SMs x 2/clk x 2 flops x "
+                                        "2.07 GHz); flops count a fused multiply-add as 2"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(r.numel() * 8),
-                    "d2h_bytes_per_step": int(z.numel() * 8),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "pipeline": "2 buffer pairs; H2D and D2H streams overlap the neighbouring steps' cycles"},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "fp64_vcycle": {"value": dofs / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms},
-            "autotune": {"seconds": t_tune, "tiles": {f"L{l}m{m}": list(v) for (l, m), v in tuned.items()}},
+            "mixed_vcycle": {
+                "value": dofs / (mixed_ms * 1e-3), "unit": UNIT, "ms_per_step": mixed_ms, "steps": args.mixed_steps,
+                "dtype": "f32 cycle (FP64 input and output)",
+                "roofline": {"bound": "hbm", "achieved": k32_bytes / (k32_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": k32_bytes / (k32_ms * 1e-3) / 1e9 / hbm_peak,
+                             "traffic": FINE_STENCIL_DRAM_BYTES.get((args.field, N, "f32")),
+                             "kernel": "finest-level FP32 stencil (Chebyshev/residual epilogues)",
+                             "launch_ms": k32_ms, "algorithmic_bytes_per_launch": k32_bytes,
+                             "launches_timed": k32_n, "peak_source": hbm_src}},
+            "autotune": {"seconds": t_tune, "fp64": {f"L{l}m{m}": list(v) for (l, m), v in tuned.items()},
+                         "mixed": {f"L{l}m{m}": list(v) for (l, m), v in tunedm.items()}},
             "solve": solve,
+            "agca_vs_dca": dca,
             "batch": batch,
         }
         print(json.dumps(line), flush=True)

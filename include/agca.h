@@ -254,10 +254,13 @@ agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
  * kernels of the V-cycle), with CUDA events on the context stream.
  * enable = 1 starts recording (up to 65536 launches); enable = 0 stops,
  * synchronizes and returns the summed kernel time in *ms, their compulsory
- * HBM bytes (element coefficients and vectors read/written once) in *bytes
- * and the number of timed launches.  Output pointers are host pointers and
- * may be NULL when enabling. */
-agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, int64_t* launches);
+ * HBM bytes (element coefficients and vectors read/written once) in *bytes,
+ * their algorithmic arithmetic in *flops (the edge form of the element
+ * action of Eq. 3.5: 129 flops per vertex for the operator plus the
+ * epilogue's, a fused multiply-add counting 2) and the number of timed
+ * launches.  Output pointers are host pointers and may be NULL. */
+agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, double* flops,
+                              int64_t* launches);
 
 /* ------------------------------------------------------------------------
  * Batched solves of many independent problems (uneven sizes allowed).

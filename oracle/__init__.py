@@ -16,8 +16,12 @@ Modules:
   stokes    Stokes operator, MINRES (Remark 6), direct solve, adjoint gradient
   fgmres    the paper's outer solver: FGMRES, block-triangular Q (Eq. 4.1), diag(A)-BFBT (Eq. 4.2)
   pointwise per-vertex rows of the fine operator for sampled checks at large sizes
+  partition the hierarchy, V-cycle and MINRES split over z-slabs, one rank per slab, with
+            interface-plane sums and all-reduced scalars (Remark 1; run as gloo ranks)
 
 Parity status: every function here is pinned by tests/test_oracle_*.py
+(partition: by tests/test_multirank_partition.py against the single-process
+oracle)
 (closed forms, invariants, brute force, library routines, convergence rates),
 except the iteration counts of the preconditioned solve, which the paper
 prints only as figures (parity unpinned for iteration counts; the solutions

@@ -57,12 +57,15 @@ def mask_matrix(A: sp.spmatrix, mrow: np.ndarray, mcol: np.ndarray) -> sp.csr_ma
     return (sp.diags(mrow) @ A @ sp.diags(mcol)).tocsr()
 
 
-def load_vector(mesh: Mesh, fbar: np.ndarray) -> np.ndarray:
-    """b_{(a,c)} = sum_T |T| fbar_c(T) / 4 for element-constant forcing, masked."""
+def load_vector(mesh: Mesh, fbar: np.ndarray, elems=None) -> np.ndarray:
+    """b_{(a,c)} = sum_T |T| fbar_c(T) / 4 for element-constant forcing, masked.
+    elems: sum over these elements only (fbar[:, i] belongs to elems[i])."""
+    if elems is None:
+        elems = np.arange(mesh.ne)
     b = np.zeros(3 * mesh.nv)
-    w = mesh.volumes / 4.0
+    w = mesh.volumes[elems] / 4.0
     for c in range(3):
-        np.add.at(b, c * mesh.nv + mesh.tets.ravel(), np.repeat(w * fbar[c], 4))
+        np.add.at(b, c * mesh.nv + mesh.tets[elems].ravel(), np.repeat(w * fbar[c], 4))
     return b * velocity_mask(mesh)
 
 
@@ -83,20 +86,24 @@ def load_vector_quadrature(mesh: Mesh, f) -> np.ndarray:
     return b * velocity_mask(mesh)
 
 
-def divergence(pmesh: Mesh, vmesh: Mesh, parent: np.ndarray) -> sp.csr_matrix:
+def divergence(pmesh: Mesh, vmesh: Mesh, parent: np.ndarray, elems=None) -> sp.csr_matrix:
     """D_kj = int psi_k div Phi_j (Eq. 3.5, second line), exact by the centroid
     rule on the velocity tets (psi_k is linear there, div Phi_j constant).
-    Shape (V_p, 3 V_v); velocity columns are not masked."""
-    G = vmesh.grads                                      # (E,4,3)
-    lam = pmesh.barycentric(parent, vmesh.centroids)     # (E,4) psi at centroid
-    pv = pmesh.tets[parent]                              # (E,4) pressure vertices
-    vol = vmesh.volumes
+    Shape (V_p, 3 V_v); velocity columns are not masked.  elems: sum over
+    these velocity elements only (parent is indexed by velocity element)."""
+    if elems is None:
+        elems = np.arange(vmesh.ne)
+    G = vmesh.grads[elems]                               # (E,4,3)
+    lam = pmesh.barycentric(parent[elems], vmesh.centroids[elems])  # (E,4) psi at centroid
+    pv = pmesh.tets[parent[elems]]                       # (E,4) pressure vertices
+    vol = vmesh.volumes[elems]
+    tv = vmesh.tets[elems]
     rows, cols, vals = [], [], []
     for m in range(4):
         for c in range(3):
             for a in range(4):
                 rows.append(pv[:, m])
-                cols.append(c * vmesh.nv + vmesh.tets[:, a])
+                cols.append(c * vmesh.nv + tv[:, a])
                 vals.append(vol * lam[:, m] * G[:, a, c])
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
@@ -104,12 +111,16 @@ def divergence(pmesh: Mesh, vmesh: Mesh, parent: np.ndarray) -> sp.csr_matrix:
     return sp.coo_matrix((vals, (rows, cols)), shape=(pmesh.nv, 3 * vmesh.nv)).tocsr()
 
 
-def pressure_mass_lumped(pmesh: Mesh, eta_fine: np.ndarray, ch: np.ndarray) -> np.ndarray:
+def pressure_mass_lumped(pmesh: Mesh, eta_fine: np.ndarray, ch: np.ndarray, elems=None) -> np.ndarray:
     """Viscosity-weighted lumped pressure mass: M_ii = sum_{T ni i} w_T |T| / 4,
-    w_T = mean of 1/eta over the 8 velocity elements refining T."""
+    w_T = mean of 1/eta over the 8 velocity elements refining T.  elems: sum
+    over these pressure elements only (row i of ch are the children of
+    elems[i], as indices into eta_fine)."""
+    if elems is None:
+        elems = np.arange(pmesh.ne)
     inv = 1.0 / eta_fine[ch]                             # (E_p, 8)
     w = ((inv[:, 0] + inv[:, 1]) + (inv[:, 2] + inv[:, 3])) + ((inv[:, 4] + inv[:, 5]) + (inv[:, 6] + inv[:, 7]))
     w = w * 0.125
     M = np.zeros(pmesh.nv)
-    np.add.at(M, pmesh.tets.ravel(), np.repeat(w * pmesh.volumes / 4.0, 4))
+    np.add.at(M, pmesh.tets[elems].ravel(), np.repeat(w * pmesh.volumes[elems] / 4.0, 4))
     return M

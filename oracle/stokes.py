@@ -64,48 +64,8 @@ class Stokes:
 
     # ---- solvers -----------------------------------------------------------
     def minres(self, b, rtol, maxit, x0=None):
-        """Preconditioned MINRES (Lanczos in the preconditioner inner product,
-        Givens QR of the tridiagonal).  Stops when the preconditioned residual
-        norm |eta| has dropped by rtol.  Returns (x, iterations)."""
-        n = len(b)
-        x = np.zeros(n) if x0 is None else x0.copy()
-        v_old = np.zeros(n)
-        v = b - self.K(x)
-        z = self.precondition(v)
-        gamma = np.sqrt(max(v @ z, 0.0))
-        gamma_old = 1.0
-        eta = gamma
-        eta0 = gamma
-        s_old = s = 0.0
-        c_old = c = 1.0
-        w_old = np.zeros(n)
-        w = np.zeros(n)
-        it = 0
-        if gamma == 0.0:
-            return x, 0
-        while it < maxit and abs(eta) > rtol * eta0:
-            it += 1
-            z = z / gamma
-            Kz = self.K(z)
-            delta = Kz @ z
-            v_new = Kz - (delta / gamma) * v - (gamma / gamma_old) * v_old
-            z_new = self.precondition(v_new)
-            gamma_new = np.sqrt(max(v_new @ z_new, 0.0))
-            a0 = c * delta - c_old * s * gamma
-            a1 = np.sqrt(a0 * a0 + gamma_new * gamma_new)
-            a2 = s * delta + c_old * c * gamma
-            a3 = s_old * gamma
-            c_new, s_new = a0 / a1, gamma_new / a1
-            w_new = (z - a3 * w_old - a2 * w) / a1
-            x = x + c_new * eta * w_new
-            eta = -s_new * eta
-            v_old, v, z = v, v_new, z_new
-            gamma_old, gamma = gamma, gamma_new
-            w_old, w = w, w_new
-            c_old, c, s_old, s = c, c_new, s, s_new
-            if gamma == 0.0:
-                break
-        return x, it
+        """Preconditioned MINRES on K with this preconditioner (see minres)."""
+        return minres(self.K, self.precondition, b, rtol, maxit, x0=x0)
 
     def solve(self, b, rtol=1e-8, inner_rtol=1e-10, maxit=2000, max_outer=20):
         """Residual refinement around MINRES until the true residual satisfies
@@ -156,3 +116,50 @@ class Stokes:
         rhs[:self.nu_] = (u - u_obs) * self.mask
         lam = self.direct(rhs) if solver == "direct" else self.solve(rhs, rtol)[0]
         return -self.element_sensitivity(lam[:self.nu_], u)
+
+
+def minres(K, precondition, b, rtol, maxit, x0=None, dot=np.dot):
+    """Preconditioned MINRES (Lanczos in the preconditioner inner product,
+    Givens QR of the tridiagonal; Remark 6's symmetric alternative to FGMRES).
+    Stops when the preconditioned residual norm |eta| has dropped by rtol.
+    dot(a, b) is the Euclidean inner product (a sum over all ranks when the
+    vectors are distributed).  Returns (x, iterations)."""
+    n = len(b)
+    x = np.zeros(n) if x0 is None else x0.copy()
+    v_old = np.zeros(n)
+    v = b - K(x)
+    z = precondition(v)
+    gamma = np.sqrt(max(dot(v, z), 0.0))
+    gamma_old = 1.0
+    eta = gamma
+    eta0 = gamma
+    s_old = s = 0.0
+    c_old = c = 1.0
+    w_old = np.zeros(n)
+    w = np.zeros(n)
+    it = 0
+    if gamma == 0.0:
+        return x, 0
+    while it < maxit and abs(eta) > rtol * eta0:
+        it += 1
+        z = z / gamma
+        Kz = K(z)
+        delta = dot(Kz, z)
+        v_new = Kz - (delta / gamma) * v - (gamma / gamma_old) * v_old
+        z_new = precondition(v_new)
+        gamma_new = np.sqrt(max(dot(v_new, z_new), 0.0))
+        a0 = c * delta - c_old * s * gamma
+        a1 = np.sqrt(a0 * a0 + gamma_new * gamma_new)
+        a2 = s * delta + c_old * c * gamma
+        a3 = s_old * gamma
+        c_new, s_new = a0 / a1, gamma_new / a1
+        w_new = (z - a3 * w_old - a2 * w) / a1
+        x = x + c_new * eta * w_new
+        eta = -s_new * eta
+        v_old, v, z = v, v_new, z_new
+        gamma_old, gamma = gamma, gamma_new
+        w_old, w = w, w_new
+        c_old, c, s_old, s = c, c_new, s, s_new
+        if gamma == 0.0:
+            break
+    return x, it

@@ -72,7 +72,8 @@ _SIGS = {
     "agca_set_coarse_projection": ([_P, _I], _I),
     "agca_flag_gradient": ([_P, _P, _D, ctypes.POINTER(_SZ)], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
-    "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)], _I),
+    "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                           ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_batch_create": ([_I, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)], _I),
     "agca_batch_destroy": ([_P], None),
     "agca_batch_last_error": ([_P], ctypes.c_char_p),
@@ -369,11 +370,11 @@ class Context:
 
     def profile_fine(self, enable: bool):
         """enable=True starts per-launch timing of the finest-level stencil
-        kernels; enable=False stops and returns (ms, bytes, launches)."""
-        ms, by, n = _D(), _D(), ctypes.c_int64()
+        kernels; enable=False stops and returns (ms, bytes, flops, launches)."""
+        ms, by, fl, n = _D(), _D(), _D(), ctypes.c_int64()
         self._check(lib().agca_profile_fine(self._h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(by),
-                                            ctypes.byref(n)), "profile_fine")
-        return ms.value, by.value, n.value
+                                            ctypes.byref(fl), ctypes.byref(n)), "profile_fine")
+        return ms.value, by.value, fl.value, n.value
 
     def level_info(self, level: int) -> LevelInfo:
         info = LevelInfo()

@@ -111,6 +111,7 @@ struct agca_ctx {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   double prof_bytes = 0.0;
+  double prof_flops = 0.0;
   int64_t prof_launches = 0;
 
   ~agca_ctx() {
@@ -314,6 +315,28 @@ double stencil_bytes(int mode, size_t s) {
   }
 }
 
+// Algorithmic arithmetic per vertex of one finest-level stencil launch (flops;
+// a fused multiply-add counts 2), from the edge form of Eq. 3.5 on a Kuhn
+// grid: per vertex 9 edge differences (3 axis edges x 3 components); per
+// tetrahedron 3 symmetrisations, 3 products eta * S off the diagonal, 3
+// products with 2 eta on it and the doubling of eta (6 x 10); the edge flux
+// sums over the 6 tetrahedra sharing each of the 3 axis edges (3 x 15); the
+// divergence of the 6 fluxes at the vertex (15): 129 in all.  The scaling by
+// h/6 folds into the epilogue (3 products, or a fused b - (h/6) y).  The
+// Chebyshev epilogues add per component: residual 2, first step 5, later
+// step 8, step from zero 7 plus 2 for its staged first iterate.
+double stencil_flops(int mode) {
+  const double op = 9.0 + 6.0 * 10.0 + 3.0 * 15.0 + 15.0;
+  switch (mode) {
+    case ST_APPLY: return op + 3.0;
+    case ST_RESID: return op + 3.0 * 2.0;
+    case ST_CHEB_FIRST: return op + 3.0 * 5.0;
+    case ST_CHEB_STEP: return op + 3.0 * 8.0;
+    case ST_CHEB_PRE: return op + 3.0 * (7.0 + 2.0);
+    default: return 0.0;
+  }
+}
+
 template <typename T>
 agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, const T* xprev, T* out, double s0,
                     double s1, double s2, double* out64 = nullptr) {
@@ -338,6 +361,7 @@ agca_status stencil(agca_ctx* ctx, int mode, int l, const T* x, const T* b, cons
     // an FP64-widened result writes 3 * (8 - sizeof(T)) more bytes per vertex
     const double wide = out64 ? 3.0 * (sizeof(double) - sizeof(T)) : 0.0;
     ctx->prof_bytes += (stencil_bytes(mode, sizeof(T)) + wide) * (double)lv.V;
+    ctx->prof_flops += stencil_flops(mode) * (double)lv.V;
     ctx->prof_launches += 1;
   }
   return AGCA_OK;
@@ -1566,7 +1590,8 @@ agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches) {
   return AGCA_OK;
 }
 
-agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, int64_t* launches) {
+agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, double* flops,
+                              int64_t* launches) {
   if (!ctx) return AGCA_EINVAL;
   if (enable) {
     const size_t want = 2 * 65536;
@@ -1577,6 +1602,7 @@ agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* byt
     }
     ctx->ev_used = 0;
     ctx->prof_bytes = 0.0;
+    ctx->prof_flops = 0.0;
     ctx->prof_launches = 0;
     ctx->prof = true;
     return AGCA_OK;
@@ -1591,6 +1617,7 @@ agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* byt
   }
   if (ms) *ms = total;
   if (bytes) *bytes = ctx->prof_bytes;
+  if (flops) *flops = ctx->prof_flops;
   if (launches) *launches = ctx->prof_launches;
   ctx->ev_used = 0;
   return AGCA_OK;

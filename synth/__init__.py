@@ -15,6 +15,7 @@ from .sinkers import (  # noqa: F401
     sphere_sinkers_on_device,
     sphere_sinkers_vertex,
     gaussian_logbumps,
+    gaussian_logbumps_on_device,
     batch_problems,
     adjoint_problem,
     random_vector,

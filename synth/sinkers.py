@@ -195,28 +195,44 @@ def sphere_sinkers_vertex(N: int, n_sinkers: int = 8, radius: float = 0.08, widt
     return eta.reshape(-1).numpy()
 
 
-def gaussian_logbumps(N: int, n_bumps: int = 20, seed: int = CONFIG_SEED0 + 2,
-                      device="cpu") -> Problem:
-    """Smooth log10-viscosity: sum of Gaussian bumps, clipped to [-3, 3];
-    forcing f_z = -(log10 mu + 3) / 6 (a constant forcing would be a pure
-    gradient and give u = 0)."""
+def _logbump_params(n_bumps: int, seed: int):
     rng = np.random.default_rng(seed)
     centres = rng.uniform(0.0, 1.0, size=(n_bumps, 3))
     amps = rng.uniform(-3.0, 3.0, size=n_bumps)
     widths = rng.uniform(0.03, 0.15, size=n_bumps)
+    return centres, amps, widths
 
+
+def _logbump_fn(centres: np.ndarray, amps: np.ndarray, widths: np.ndarray):
     def fn(x):
         c = torch.as_tensor(centres, dtype=torch.float64, device=x.device)
         lg = torch.zeros_like(x[..., 0])
-        for k in range(n_bumps):
+        for k in range(len(amps)):
             r2 = ((x - c[k]) ** 2).sum(dim=-1)
             lg = lg + float(amps[k]) * torch.exp(-r2 / (2.0 * float(widths[k]) ** 2))
         lg = lg.clamp(-3.0, 3.0)
         return torch.pow(10.0, lg), -(lg + 3.0) / 6.0
 
-    eta, fbar = _element_means(N, fn, "quad4", _device(device), 1)
+    return fn
+
+
+def gaussian_logbumps(N: int, n_bumps: int = 20, seed: int = CONFIG_SEED0 + 2,
+                      device="cpu") -> Problem:
+    """Smooth log10-viscosity: sum of Gaussian bumps (centres uniform in
+    [0, 1]^3, amplitudes uniform in [-3, 3], widths uniform in [0.03, 0.15]),
+    clipped to [-3, 3]; forcing f_z = -(log10 mu + 3) / 6 (a constant forcing
+    would be a pure gradient and give u = 0)."""
+    centres, amps, widths = _logbump_params(n_bumps, seed)
+    eta, fbar = _element_means(N, _logbump_fn(centres, amps, widths), "quad4", _device(device), 1)
     return Problem(N, eta, fbar, dict(kind="logbumps", centres=centres, amps=amps,
                                       widths=widths, seed=seed))
+
+
+def gaussian_logbumps_on_device(N: int, n_bumps: int = 20, seed: int = CONFIG_SEED0 + 2, device="cuda"):
+    """The gaussian_logbumps field generated and kept on the device: (eta (E,),
+    fbar (3, E)) float64 tensors (the host copies at N = 128 would be 3 GB)."""
+    centres, amps, widths = _logbump_params(n_bumps, seed)
+    return _element_means_on_device(N, _logbump_fn(centres, amps, widths), device)
 
 
 def batch_problems(seed: int = CONFIG_SEED0 + 3, sizes=(32, 48, 64), per_size: int = 8,

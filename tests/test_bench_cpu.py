@@ -25,8 +25,28 @@ def test_levels_match_library(bench):
 
 
 def test_config_of_both_arms(bench):
-    cfg = bench.arm_config(64, 6, [118, 531, 2698, 14302, 11052], 1)
-    assert cfg["N_pressure"] == 64 and cfg["velocity_cubes"] == 128 and cfg["levels"] == 6
-    assert cfg["velocity_dofs"] == 3 * 129 ** 3 == 6440067
+    cfg = bench.arm_config("logbump", 128, 7, [0, 1, 2, 3, 4, 5], 1)
+    assert cfg["N_pressure"] == 128 and cfg["velocity_cubes"] == 256 and cfg["levels"] == 7
+    assert cfg["velocity_dofs"] == 3 * 257 ** 3 == 50923779
+    assert cfg["pressure_dofs"] == 129 ** 3 == 2146689
     assert cfg["parallelism"] == "replicas1" and cfg["global_batch"] == 1
-    assert 0 < bench.FINE_STENCIL_DRAM_BYTES < 3 * 60 * 129 ** 3
+    assert "128^3 pressure cubes" in cfg["workload"]
+
+
+def test_fp64_peak_from_unit_counts(bench):
+    # 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz, the nominal 1.25 TFLOP/s
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-4
+
+
+def test_reference_arm_names_the_size_it_times(bench, capsys):
+    class A:
+        steps, warmup, gpus, field, N = 1, 0, 1, "logbump", 128
+
+    assert bench.run_reference(A()) == 0
+    import json
+
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["N_pressure"] == 16
+    assert line["config"]["velocity_dofs"] == 3 * 33 ** 3
+    assert "128^3" in line["config"]["sample_of"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"

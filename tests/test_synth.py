@@ -29,3 +29,13 @@ def test_vertex_values_are_the_field_at_the_vertices():
     pts = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
     d = np.min(np.linalg.norm(pts[:, None, :] - centres[None], axis=2), axis=1)
     assert np.argmax(v) == np.argmin(d)
+
+
+def test_on_device_logbumps_match_host_generator():
+    from synth import gaussian_logbumps, gaussian_logbumps_on_device
+
+    p = gaussian_logbumps(5, n_bumps=6, seed=4)
+    eta, fbar = gaussian_logbumps_on_device(5, n_bumps=6, seed=4, device="cpu")
+    assert np.array_equal(eta.numpy(), p.eta)
+    assert np.array_equal(fbar.numpy(), p.fbar)
+    assert p.eta.min() >= 1e-3 * (1 - 1e-12) and p.eta.max() <= 1e3 * (1 + 1e-12)
