@@ -400,6 +400,66 @@ def agca_vs_dca(pkg, dev, stream):
     return out
 
 
+def coefficient_study(pkg, dev, stream, N=32):
+    """The axes of the paper's convergence study (Sec. 4, Figs. 7-9) at
+    32^3 pressure cubes, mixed solves to 1e-8:
+    * coefficient approximations (Sec. 3.2) on the unaligned cube eta_2 with
+      DR 1e6: the finest coefficient by the 4-point rule (analytic) or as
+      the mean of the P1 interpolant, the coarse DCA coefficient analytic on
+      the coarse elements, P1 on the coarse grid, or the arithmetic /
+      harmonic / geometric projection of the children; each with pure DCA
+      and with AGCA at nu = 10;
+    * the threshold nu on the tanh cube eta_3 (omega 10, DR 1e6, Fig. 9):
+      flagged elements, stored Galerkin bytes and iterations."""
+    from synth import cube_field, field_problem, level_coefficients, p1_element_means
+
+    L = bench_levels(N)
+
+    def run(eta, fbar, nu, proj=0, lc=None):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
+        c.set_viscosity(eta)
+        c.set_coarse_projection(proj)
+        gbytes = c.flag(nu)
+        for l, v in (lc or {}).items():
+            c.set_level_coefficient(l, torch.from_numpy(v).to(dev))
+        c.setup()
+        b = c.load_vector(fbar)
+        try:
+            _, its, rel = c.solve(b, 1e-8, 20000)
+        except pkg.AgcaError as e:
+            if e.status != 4:
+                raise
+            its, rel = 20000, float("nan")
+        torch.cuda.synchronize(dev)
+        out = {"minres_iters": its, "relres": rel, "time_to_1e-8_s": time.perf_counter() - t0,
+               "flagged": int(sum(c.level_info(l).n_flag for l in range(1, L))), "galerkin_store_bytes": gbytes}
+        del c
+        return out
+
+    out = {"N_pressure": N, "levels": L}
+    fn2 = cube_field("unaligned", 1e6)
+    p2 = field_problem(N, fn2)
+    fbar2 = torch.from_numpy(p2.fbar.ravel()).to(dev)
+    eta_q = torch.from_numpy(p2.eta).to(dev)
+    eta_p1 = torch.from_numpy(p1_element_means(2 * N, fn2)).to(dev)
+    variants = {"analytic": (eta_q, 0, level_coefficients(fn2, N, L, "analytic")),
+                "p1": (eta_p1, 0, level_coefficients(fn2, N, L, "p1")),
+                "arithmetic": (eta_q, 0, None), "harmonic": (eta_q, 1, None), "geometric": (eta_q, 2, None)}
+    approx = {}
+    for name, (eta, proj, lc) in variants.items():
+        approx[name] = {"dca": run(eta, fbar2, NU_DCA, proj, lc), "agca_nu10": run(eta, fbar2, NU, proj, lc)}
+    out["approximations_unaligned_cube_dr1e6"] = approx
+    fn3 = cube_field("tanh", 1e6, omega=10.0)
+    p3 = field_problem(N, fn3)
+    eta3 = torch.from_numpy(p3.eta).to(dev)
+    fbar3 = torch.from_numpy(p3.fbar.ravel()).to(dev)
+    out["nu_sweep_tanh_cube_omega10_dr1e6"] = {f"{nu:g}": run(eta3, fbar3, nu) for nu in (1.5, 3.0, 10.0, 100.0,
+                                                                                         1e4, NU_DCA)}
+    return out
+
+
 def run_batch(args, dev, stream):
     """The 24-problem batch (uneven 32^3/48^3/64^3 single sinkers): batched
     V-cycle throughput against the same problems cycled one by one, and
@@ -487,6 +547,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-dca", action="store_true")
+    ap.add_argument("--no-study", action="store_true", help="skip the coefficient / nu study at 32^3")
     ap.add_argument("--batch-n", type=int, default=0)
     ap.add_argument("--cycles-only", action="store_true",
                     help="profiling aid: warm-up and timed cycles of both precisions only, one short JSON line")
@@ -584,6 +645,7 @@ def main():
     if not args.no_solve and not args.no_dca:
         dca = agca_vs_dca(pkg, dev, stream)
     batch = run_batch(args, dev, stream) if not args.no_batch else None
+    study = coefficient_study(pkg, dev, stream) if not (args.no_solve or args.no_study) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -629,6 +691,7 @@ def main():
                          "mixed": {f"L{l}m{m}": list(v) for (l, m), v in tunedm.items()}},
             "solve": solve,
             "agca_vs_dca": dca,
+            "coefficient_study": study,
             "batch": batch,
         }
         print(json.dumps(line), flush=True)

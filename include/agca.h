@@ -146,6 +146,19 @@ agca_status agca_flag_gradient(agca_ctx* ctx, const double* eta_vertex_dev, doub
 /* Bind caller-owned device memory for the stored Galerkin matrices. */
 agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes);
 
+/* Direct coarse-grid approximation with a coefficient evaluated on the coarse
+ * grid itself (Eq. 2.5; the coefficient approximations of Sec. 3.2): replace
+ * the DCA coefficient of coarse level 1 <= level < L by coef_dev
+ * (double[E_level], device, element order as on the finest level, every
+ * value finite and > 0), e.g. the analytic viscosity's mean over the coarse
+ * element's quadrature points or the mean of its P1 interpolant on the
+ * coarse grid.  Call after agca_flag (which projects the children's means)
+ * and before agca_setup; the flags and the per-element maxima and minima
+ * stay those of the finest descendants, and coarser levels keep the
+ * coefficients agca_flag projected.  Copies asynchronously on the context
+ * stream.  AGCA_ESTATE before agca_flag; AGCA_EINVAL for a bad level. */
+agca_status agca_set_level_coefficient(agca_ctx* ctx, int level, const double* coef_dev);
+
 /* Assemble the local Galerkin matrices of all flagged elements, finest to
  * coarsest (Eqs. 2.6-2.7, Eq. B.2), the level diagonals, lambda_hat per level,
  * the dense Cholesky factor of the coarsest operator and the pressure mass.

@@ -100,7 +100,7 @@ class Hierarchy:
     def __init__(self, N: int, L: int, eta: np.ndarray, nu: float = 10.0,
                  cheb_lo: float = 0.1, cheb_hi: float = 1.1, cheb_degree: int = 2,
                  power_iters: int = 20, build_operators: bool = True, projection: str = "arithmetic",
-                 eta_vertex: np.ndarray | None = None):
+                 eta_vertex: np.ndarray | None = None, level_coef: dict | None = None):
         nL = 2 * N
         assert nL % (1 << (L - 1)) == 0 and (nL >> (L - 1)) >= 2
         self.N, self.L, self.nu = N, L, nu
@@ -120,6 +120,13 @@ class Hierarchy:
             self.flags[l] = self.mx[l] > nu * self.mn[l]
         if eta_vertex is not None:  # the gradient rule of Eq. 2.8 instead of the ratio rule
             self.flags = gradient_flags(N, L, eta_vertex, nu)[1]
+        # DCA coefficient of coarse levels evaluated by the caller (Eq. 2.5 with
+        # the analytic coefficient at the coarse element's quadrature points,
+        # or the mean of its P1 interpolant, Sec. 3.2) instead of projected
+        # from the children; flags keep the finest descendants' max/min
+        for l, c in (level_coef or {}).items():
+            assert 1 <= l < L and np.shape(c) == (self.mesh[l].ne,)
+            self.mean[l] = np.asarray(c, dtype=np.float64)
         self.flist = {l: np.nonzero(self.flags[l])[0] for l in range(1, L)}
         self.findex = {}
         for l in range(1, L):
@@ -276,14 +283,24 @@ KUHN_OFFSETS = np.array([(0, 0, 0)] + [s * np.array(d) for d in
                          for s in (1, -1)], dtype=np.int64)
 
 
-def stencil_blocks(H: Hierarchy, l: int) -> np.ndarray:
-    """The level-l operator as per-vertex stencils (Remark 5): out[v, o, c, d]
-    is the coupling of component c at vertex v with component d at vertex
-    v + KUHN_OFFSETS[o] (zero where the neighbour is outside the grid), read
-    from the assembled global matrix."""
+def flagged_operator(H: Hierarchy, l: int):
+    """The stored-Galerkin part of the level-l AGCA operator: the assembly of
+    the flagged elements' matrices only (Eq. 2.9's second sum), Dirichlet
+    rows and columns masked."""
+    m = H.mesh[l]
+    A = fem.assemble(m, H.gca[l], H.flist[l]) if len(H.flist[l]) else sp.csr_matrix((3 * m.nv, 3 * m.nv))
+    return fem.mask_matrix(A, H.mask[l], H.mask[l])
+
+
+def stencil_blocks(H: Hierarchy, l: int, A=None) -> np.ndarray:
+    """The level-l operator (or the matrix A on the level's DoFs) as
+    per-vertex stencils (Remark 5): out[v, o, c, d] is the coupling of
+    component c at vertex v with component d at vertex v + KUHN_OFFSETS[o]
+    (zero where the neighbour is outside the grid), read from the assembled
+    global matrix."""
     m = H.mesh[l]
     n1 = m.n + 1
-    A = H.A[l].tocsr()
+    A = (H.A[l] if A is None else A).tocsr()
     out = np.zeros((m.nv, len(KUHN_OFFSETS), 3, 3))
     for o, d in enumerate(KUHN_OFFSETS):
         nb = m.ijk + d

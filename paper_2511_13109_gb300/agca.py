@@ -70,6 +70,7 @@ _SIGS = {
     "agca_set_tile_config": ([_P, _I, _I, _I, _I], _I),
     "agca_stencil_tiles": ([_I, _I, _I, ctypes.POINTER(_I)], _I),
     "agca_set_coarse_projection": ([_P, _I], _I),
+    "agca_set_level_coefficient": ([_P, _I, _P], _I),
     "agca_flag_gradient": ([_P, _P, _D, ctypes.POINTER(_SZ)], _I),
     "agca_launch_count": ([_P, ctypes.POINTER(ctypes.c_int64)], _I),
     "agca_profile_fine": ([_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
@@ -258,6 +259,12 @@ class Context:
         self.gca_store = torch.empty(int(b.value), dtype=torch.uint8, device=self.device)
         self._check(lib().agca_bind_gca_store(self._h, _ptr(self.gca_store), b.value), "bind_gca_store")
         return int(b.value)
+
+    def set_level_coefficient(self, level: int, coef: torch.Tensor):
+        """DCA coefficient of a coarse level evaluated on that level (see
+        agca_set_level_coefficient); after flag(), before setup()."""
+        _need(coef, self.E[level] if 1 <= level < self.L else -1, torch.float64, "coef")
+        self._check(lib().agca_set_level_coefficient(self._h, int(level), _ptr(coef)), "set_level_coefficient")
 
     def setup(self):
         self._check(lib().agca_setup(self._h), "setup")

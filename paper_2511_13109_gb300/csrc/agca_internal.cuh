@@ -79,6 +79,7 @@ struct LevelOp {
   const int32_t* list; // flagged element ids (coarse levels)
   int64_t n_flag;      // number of flagged elements
   T* ye;               // n_flag * 12 scratch: s_e A_e x_e of the flagged elements
+  const T* hedge;      // finest FP64 level: per-vertex edge sums of eta [3][V] (edge form), or nullptr
 };
 
 __host__ __device__ inline int64_t nverts(int n) { return (int64_t)(n + 1) * (n + 1) * (n + 1); }
@@ -161,6 +162,14 @@ struct TileGrid {
 };
 TileGrid stencil_tiles(int n, int by, int zch_req);
 
+// FP64 finest-level operator in edge form (stencil_edge.cu): modes APPLY,
+// RESID and the Chebyshev steps, with op.hedge = the per-vertex sums of eta
+// over the 6 tetrahedra around each forward axis edge (launch_edge_sums)
+TileGrid edge_tiles(int n, int zch_req);
+cudaError_t launch_edge_sums(int n, const double* eta, double* hedge, cudaStream_t s);
+cudaError_t launch_stencil_edge(int mode, const LevelOp<double>& op, const StencilArgs<double>& a, cudaStream_t s,
+                                int zch_req);
+
 // ------------------------------------------------------------ batched forms
 // One (problem, level) operator application inside a batched launch.
 template <typename TS, typename T>
@@ -177,6 +186,14 @@ struct StencilTask {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s);
+// the edge form for a batch of FP64 finest-level tasks (tiles from edge_tiles)
+cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<double, double>* tasks, int ntasks, int64_t ntiles,
+                                      cudaStream_t s);
+// whether a batched step of this kind runs the edge form
+template <typename TS, typename T>
+constexpr bool edge_form_step(int mode, bool coarse) {
+  return sizeof(TS) == 8 && sizeof(T) == 8 && !coarse && mode != ST_STOKES;
+}
 
 // Element-wise batched tasks (transfers, conversions, coarsest solves).
 struct XferTask {

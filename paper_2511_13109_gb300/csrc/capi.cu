@@ -34,6 +34,7 @@ struct Level {
   int32_t* list = nullptr;
   int64_t n_flag = 0;
   double* gca64 = nullptr;
+  double* hedge = nullptr;  // FP64 finest level: per-vertex edge sums of eta [3][V] (edge-form operator)
   double* diag = nullptr;
   double* invD64 = nullptr;
   // FP32 copies (mixed)
@@ -187,6 +188,7 @@ void carve_workspace(agca_ctx* ctx, char* base) {
       lv.mn = lv.mean;
     }
     if (mixed) lv.mean32 = cv.take<float>(lv.E);
+    if (!mixed && l == ctx->L) lv.hedge = cv.take<double>(3 * lv.V);
     lv.diag = cv.take<double>(3 * lv.V);
     lv.invD64 = cv.take<double>(3 * lv.V);
     if (mixed) lv.invD32 = cv.take<float>(3 * lv.V);
@@ -237,6 +239,7 @@ LevelOp<double> op64(const agca_ctx* ctx, int l) {
   op.h6 = 1.0 / (6.0 * lv.n);
   op.hq = 1.0 / (6.0 * (double)lv.n * lv.n);
   op.coef = lv.mean;
+  if (l == ctx->L) op.hedge = lv.hedge;
   if (l < ctx->L) {
     op.fidx = lv.fidx;
     op.gca = lv.gca64;
@@ -914,7 +917,7 @@ void push_stencil(agca_batch* b, std::vector<BatchStep>& steps, int mode, bool c
   const int zch = (int)std::min<int64_t>(32, std::max<int64_t>(4, (cols + slots - 1) / slots));
   int64_t tiles = 0, gca = 0;
   for (auto& tk : t) {
-    tk.tg = stencil_tiles(tk.op.n, 8, zch);
+    tk.tg = edge_form_step<TS, T>(mode, coarse) ? edge_tiles(tk.op.n, zch) : stencil_tiles(tk.op.n, 8, zch);
     tk.tile0 = tiles;
     tiles += (int64_t)tk.tg.per_z() * tk.tg.gz;
     gca = std::max<int64_t>(gca, tk.op.n_flag * 12);
@@ -1313,6 +1316,7 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
   if (!ctx->ws) return ctx->fail(AGCA_ESTATE, "bind the workspace first");
   Level& lf = ctx->lev[ctx->L];
   CK(cudaMemcpyAsync(lf.mean, eta_dev, lf.E * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (lf.hedge) LK(1, launch_edge_sums(lf.n, lf.mean, lf.hedge, ctx->stream));
   ctx->have_eta = true;
   ctx->flagged = ctx->setup_done = false;
   return AGCA_OK;
@@ -1378,6 +1382,20 @@ agca_status agca_bind_gca_store(agca_ctx* ctx, void* dev_ptr, size_t bytes) {
   ctx->gs = static_cast<char*>(dev_ptr);
   ctx->gs_bytes = bytes;
   carve_gca(ctx, ctx->gs);
+  return AGCA_OK;
+}
+
+agca_status agca_set_level_coefficient(agca_ctx* ctx, int level, const double* coef_dev) {
+  if (!ctx || !coef_dev) return AGCA_EINVAL;
+  if (level < 1 || level >= ctx->L) return ctx->fail(AGCA_EINVAL, "level must be a coarse level");
+  if (!ctx->flagged) return ctx->fail(AGCA_ESTATE, "flag first");
+  ctx->clear_graphs();
+  Level& lv = ctx->lev[level];
+  CK(cudaMemcpyAsync(lv.mean, coef_dev, lv.E * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  LK(1, launch_check_eta(lv.mean, lv.E, ctx->status, ctx->stream));
+  CKS(check_status(ctx, "agca_set_level_coefficient"));
+  ctx->setup_done = false;
   return AGCA_OK;
 }
 

@@ -675,6 +675,11 @@ TileGrid stencil_tiles(int n, int BY, int zch_req) {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s) {
+  if constexpr (sizeof(TS) == 8 && sizeof(T) == 8) {
+    if (edge_form_step<TS, T>(mode, coarse))
+      return launch_stencil_edge_batch(mode, reinterpret_cast<const StencilTask<double, double>*>(tasks), ntasks,
+                                       ntiles, s);
+  }
   if (coarse) return launch_batch_mode<TS, T, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
   return launch_batch_mode<TS, T, 8, false>(mode, tasks, ntasks, ntiles, 0, s);
 }
@@ -689,6 +694,12 @@ template <typename TS, typename T>
 cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s,
                            const TileCfg* cfg) {
   const int by = cfg ? cfg->by : 8, zch = cfg ? cfg->zch : 0;
+  if constexpr (sizeof(T) == 8 && sizeof(TS) == 8) {
+    // the FP64 finest level runs the edge form when its edge sums exist
+    if (!op.fidx && op.hedge && mode != ST_STOKES)
+      return launch_stencil_edge(mode, reinterpret_cast<const LevelOp<double>&>(op),
+                                 reinterpret_cast<const StencilArgs<double>&>(a), s, zch);
+  }
   if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
     if (by == 12) {
       if (op.fidx) return launch_mode<TS, T, 12, true>(mode, op, a, s, zch);

@@ -17,6 +17,12 @@ from .sinkers import (  # noqa: F401
     gaussian_logbumps,
     gaussian_logbumps_on_device,
     batch_problems,
+    C_UA,
+    cube_field,
+    sphere_field,
+    field_problem,
+    p1_element_means,
+    level_coefficients,
     adjoint_problem,
     random_vector,
     velocity_grid,

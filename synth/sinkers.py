@@ -235,6 +235,81 @@ def gaussian_logbumps_on_device(N: int, n_bumps: int = 20, seed: int = CONFIG_SE
     return _element_means_on_device(N, _logbump_fn(centres, amps, widths), device)
 
 
+# centre of the grid-unaligned shapes of Section 3.2
+C_UA = 11.0 / 24.0
+
+
+def cube_field(kind: str, dr: float, omega: float = 10.0):
+    """The cube viscosities of Eqs. 3.6-3.9 as a field function x -> (eta,
+    f_z): "aligned" (eta_1, the cube of half-width 1/8 around 1/2), "unaligned"
+    (eta_2, around C_UA = 11/24) or "tanh" (eta_3, the product of the 1-D tanh
+    profiles of Eq. 3.7 around C_UA with smoothing omega); eta = eta_low +
+    (eta_high - eta_low) xi with eta_high/low = DR^(+-1/2), f = (0, 0, -xi)."""
+    eta_hi, eta_lo = dr ** 0.5, dr ** -0.5
+    r = 0.125
+
+    def fn(x):
+        if kind == "tanh":
+            xi = torch.ones_like(x[..., 0])
+            for a in range(3):
+                xi = xi * 0.5 * (torch.tanh(omega * (x[..., a] - (C_UA - r))) - torch.tanh(omega * (x[..., a] - (C_UA + r))))
+        else:
+            c = 0.5 if kind == "aligned" else C_UA
+            xi = ((x - c).abs() <= r).all(dim=-1).to(torch.float64)
+        return eta_lo + (eta_hi - eta_lo) * xi, -xi
+
+    return fn
+
+
+def sphere_field(centres: np.ndarray, radii: np.ndarray, width: float, dr: float):
+    """Union of tanh-smoothed balls as a field function x -> (eta, f_z)."""
+    return _tanh_spheres_fn(np.asarray(centres, dtype=np.float64), np.asarray(radii, dtype=np.float64), width, dr)
+
+
+def field_problem(N: int, fn, kind: str = "field", device="cpu") -> Problem:
+    """Element means (4-point rule) of a field function on the finest grid."""
+    eta, fbar = _element_means(N, fn, "quad4", _device(device), 1)
+    return Problem(N, eta, fbar, dict(kind=kind))
+
+
+def p1_element_means(n: int, fn) -> np.ndarray:
+    """Mean over each Kuhn tetrahedron of a grid with n cubes per axis of the
+    P1 interpolant of the field (its values at the grid vertices): the mean
+    of a linear function is the average of its 4 vertex values."""
+    g = torch.arange(n + 1, dtype=torch.float64) / n
+    K, J, I = torch.meshgrid(g, g, g, indexing="ij")
+    vals, _ = fn(torch.stack([I, J, K], dim=-1))
+    vals = vals.numpy()                                  # [k][j][i]
+    out = np.zeros((n, n, n, 6))
+    for t, p in enumerate(PERMS):
+        corner = np.zeros(3, dtype=np.int64)
+        acc = vals[:n, :n, :n].copy()
+        for a in range(3):
+            corner[p[a]] += 1
+            acc = acc + vals[corner[2]:corner[2] + n, corner[1]:corner[1] + n, corner[0]:corner[0] + n]
+        out[..., t] = acc * 0.25
+    return out.reshape(-1)
+
+
+def level_coefficients(fn, N: int, L: int, mode: str = "analytic") -> dict:
+    """Coefficients of the coarse levels l = 1..L-1 (level l has 2N / 2^(L-l)
+    cubes per axis) evaluated on the level's own elements, for direct coarse
+    approximation (Eq. 2.5): "analytic" = the field's mean over the 4-point
+    rule of the coarse element, "p1" = the mean of its P1 interpolant on the
+    coarse grid (Sec. 3.2)."""
+    out = {}
+    for l in range(1, L):
+        n = (2 * N) >> (L - l)
+        if mode == "analytic":
+            assert n % 2 == 0
+            out[l], _ = _element_means(n // 2, fn, "quad4", "cpu", 1)
+        elif mode == "p1":
+            out[l] = p1_element_means(n, fn)
+        else:
+            raise ValueError(mode)
+    return out
+
+
 def batch_problems(seed: int = CONFIG_SEED0 + 3, sizes=(32, 48, 64), per_size: int = 8,
                    device="cpu", generate=True):
     """Independent single-sphere problems of uneven sizes: centre uniform in

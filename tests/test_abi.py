@@ -53,6 +53,8 @@ def test_host_only_calls(libagca):
     assert L.agca_bind_workspace(h, ctypes.c_void_p(256), 16) == 2
     # calls out of order report a state error
     assert L.agca_setup(h) == 7
+    assert L.agca_set_level_coefficient(h, 1, ctypes.c_void_p(256)) == 7   # before agca_flag
+    assert L.agca_set_level_coefficient(h, 4, ctypes.c_void_p(256)) == 1   # the finest level is not coarse
     assert L.agca_set_smoother(h, 1, 0.3, 1.2, 20) == 1
     assert b"smoother" in L.agca_last_error(h)
     assert L.agca_set_solver_options(h, 0.0, 4) == 1

@@ -212,3 +212,106 @@ def test_agca_rows_fit_the_15_point_kuhn_stencil():
         y = agca.stencil_apply(H, l, blocks, x)
         assert np.allclose(y, H.A[l] @ x, rtol=0, atol=1e-12 * np.abs(H.A[l] @ x).max()), l
     assert len(agca.KUHN_OFFSETS) == 15 and len({tuple(o) for o in agca.KUHN_OFFSETS}) == 15
+
+
+# ---- coarse coefficients evaluated on the coarse grid (Eq. 2.5, Sec. 3.2) ----
+def test_level_coefficient_override():
+    """Overriding a coarse level's DCA coefficient with the values the
+    children's projection gives changes nothing; with every element DCA
+    (no flags) the level operator is the assembly of the rediscretised
+    element matrices of the given coefficient."""
+    from oracle import fem
+    from synth import sphere_sinkers
+
+    p = sphere_sinkers(4, 3, 0.15, 0.02, 1e4)
+    H = agca.Hierarchy(4, 3, p.eta, 10.0)
+    H2 = agca.Hierarchy(4, 3, p.eta, 10.0, level_coef={1: H.mean[1].copy(), 2: H.mean[2].copy()})
+    for l in (1, 2, 3):
+        assert (H.A[l] != H2.A[l]).nnz == 0
+    rng = np.random.default_rng(3)
+    c = {l: np.exp(rng.normal(size=H.mesh[l].ne)) for l in (1, 2)}
+    Hd = agca.Hierarchy(4, 3, p.eta, 1e300, level_coef=c)
+    for l in (1, 2):
+        m = Hd.mesh[l]
+        A = fem.assemble(m, fem.element_matrices(m, c[l]))
+        ref = fem.mask_matrix(A, Hd.mask[l], Hd.mask[l])
+        assert abs(Hd.A[l] - ref).max() <= 1e-13 * abs(ref).max()
+    # flags keep the finest descendants' extremes
+    assert all(np.array_equal(Hd.flags[l], H.mx[l] > 1e300 * H.mn[l]) for l in (1, 2))
+
+
+def test_analytic_level_coefficients_of_quadratic_field_equal_the_projection():
+    """The 4-point rule integrates quadratics exactly, and a parent's mean is
+    the average of its 8 equal-volume children's means: for a quadratic
+    field the analytic coarse coefficients equal the arithmetic projection."""
+    import torch
+
+    from synth import field_problem, level_coefficients
+
+    def fn(x):
+        v = 1.0 + x[..., 0] ** 2 + 2.0 * x[..., 1] * x[..., 2] + 0.5 * x[..., 2]
+        return v, torch.zeros_like(v)
+
+    N, L = 4, 3
+    p = field_problem(N, fn)
+    mean, _, _, _ = agca.flag_hierarchy(N, L, p.eta, 10.0)
+    lc = level_coefficients(fn, N, L, "analytic")
+    for l in (1, 2):
+        assert np.abs(lc[l] - mean[l]).max() <= 1e-14 * np.abs(mean[l]).max()
+
+
+def test_p1_means_of_linear_field_are_exact_means():
+    import torch
+
+    from synth import field_problem, p1_element_means
+
+    def fn(x):
+        v = 2.0 + 3.0 * x[..., 0] - x[..., 1] + 0.25 * x[..., 2]
+        return v, torch.zeros_like(v)
+
+    p = field_problem(3, fn)
+    assert np.abs(p1_element_means(6, fn) - p.eta).max() <= 1e-14 * np.abs(p.eta).max()
+
+
+def test_tanh_cube_tends_to_the_unaligned_cube():
+    """eta_3 (Eq. 3.7 profiles) approaches eta_2 away from the cube faces as
+    omega grows; eta_1 is the aligned cube of cfg0."""
+    import torch
+
+    from synth import C_UA, cube_field
+
+    pts = torch.tensor([[C_UA, C_UA, C_UA], [0.1, 0.2, 0.9], [C_UA + 0.1, C_UA - 0.1, C_UA], [0.5, 0.5, 0.5]],
+                       dtype=torch.float64)
+    e2, f2 = cube_field("unaligned", 1e6)(pts)
+    e3, _ = cube_field("tanh", 1e6, omega=1e3)(pts)
+    assert torch.allclose(e3, e2, rtol=1e-9)
+    assert float(e2[0]) == 1e3 and float(e2[1]) == 1e-3 and float(f2[0]) == -1.0
+    e1, _ = cube_field("aligned", 1e6)(pts)
+    assert float(e1[3]) == 1e3 and float(e1[1]) == 1e-3
+
+
+def test_flagged_stencils_plus_dca_part_rebuild_the_level_operator():
+    """Remark 5's storage for AGCA: per-vertex 15-offset stencils of the
+    flagged elements' Galerkin matrices only, plus the matrix-free DCA part of
+    the unflagged elements, apply as the level operator; the stencils are
+    nonzero only at vertices of flagged elements."""
+    from oracle import fem
+    from synth import sphere_sinkers
+
+    p = sphere_sinkers(4, 3, 0.15, 0.02, 1e4)
+    H = agca.Hierarchy(4, 3, p.eta, 10.0)
+    for l in (1, 2):
+        m = H.mesh[l]
+        assert len(H.flist[l]) > 0
+        S = agca.stencil_blocks(H, l, agca.flagged_operator(H, l))
+        unflagged = np.setdiff1d(np.arange(m.ne), H.flist[l])
+        Ad = fem.mask_matrix(fem.assemble(m, fem.element_matrices(m, H.mean[l][unflagged], unflagged), unflagged),
+                             H.mask[l], H.mask[l])
+        x = np.random.default_rng(l).normal(size=3 * m.nv)
+        y = agca.stencil_apply(H, l, S, x) + Ad @ x
+        ref = H.A[l] @ x
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+        touched = np.zeros(m.nv, dtype=bool)
+        touched[m.tets[H.flist[l]].ravel()] = True
+        assert np.abs(S[~touched]).max() == 0.0
+        assert np.abs(S[touched & m.interior]).max(axis=(1, 2, 3)).min() > 0.0
