@@ -457,6 +457,33 @@ def coefficient_study(pkg, dev, stream, N=32):
     fbar3 = torch.from_numpy(p3.fbar.ravel()).to(dev)
     out["nu_sweep_tanh_cube_omega10_dr1e6"] = {f"{nu:g}": run(eta3, fbar3, nu) for nu in (1.5, 3.0, 10.0, 100.0,
                                                                                          1e4, NU_DCA)}
+    # the paper's outer solver (Sec. 4) against MINRES on the unaligned cube,
+    # AGCA with the analytic coarse coefficient (where DCA fails)
+    lc = level_coefficients(fn2, N, L, "analytic")
+    c = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
+    c.set_viscosity(eta_q)
+    c.flag(NU)
+    for l, v in lc.items():
+        c.set_level_coefficient(l, torch.from_numpy(v).to(dev))
+    c.setup()
+    b = c.load_vector(fbar2)
+    solvers = {}
+    for name, call in (("minres_blockdiag_mass", lambda: c.solve(b, 1e-8, 20000)),
+                       ("fgmres_blocktri_mass_restart50", lambda: c.solve_fgmres(b, 1e-8, 20000, 50, "mass")),
+                       ("fgmres_blocktri_bfbt_restart50_zcg10", lambda: c.solve_fgmres(b, 1e-8, 20000, 50, "bfbt", 10)),
+                       ("fgmres_blocktri_bfbt_restart50_zcg40", lambda: c.solve_fgmres(b, 1e-8, 20000, 50, "bfbt", 40))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        try:
+            _, its, rel = call()
+        except pkg.AgcaError as e:
+            if e.status != 4:
+                raise
+            its, rel = 20000, float("nan")
+        torch.cuda.synchronize(dev)
+        solvers[name] = {"iters": its, "relres": rel, "solve_s": time.perf_counter() - t0}
+    out["outer_solvers_unaligned_cube_dr1e6_analytic_agca"] = solvers
+    del c
     return out
 
 

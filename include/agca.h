@@ -72,7 +72,12 @@ typedef enum {
   AGCA_FIELD_GCA = 5,    /* double[n_flag*144]: stored Galerkin matrices, list order */
   AGCA_FIELD_DIAG = 6,   /* double[3*V_l]: diagonal of the level operator (0 on boundary) */
   AGCA_FIELD_COARSE = 7, /* double[m*m]: dense coarsest operator on interior DoFs (level 1 only) */
-  AGCA_FIELD_PMASS = 8   /* double[(N+1)^3]: viscosity-weighted lumped pressure mass (level L-1) */
+  AGCA_FIELD_PMASS = 8,  /* double[(N+1)^3]: viscosity-weighted lumped pressure mass (level L-1) */
+  AGCA_FIELD_SIDX = 9,   /* int32[V_l]: stencil index of a vertex touched by a flagged element, else -1
+                            (coarse levels, after agca_flag; touched vertices numbered in ascending order) */
+  AGCA_FIELD_STENCIL = 10 /* double[n_stencil*135]: per touched vertex, the stored-Galerkin part of the
+                            level operator as 15 Kuhn-offset blocks of 3x3 couplings, [offset][row c][column d],
+                            offsets 0, +-x, +-y, +-z, +-(x+y), +-(x+z), +-(y+z), +-(x+y+z) (Remark 5) */
 } agca_field;
 
 typedef struct {
@@ -81,6 +86,7 @@ typedef struct {
   int64_t elements; /* E_l */
   int64_t n_flag;   /* flagged elements (0 on the finest level) */
   double lambda;    /* power-iteration estimate of lambda_max(D^-1 A_l) (0 on level 1) */
+  int64_t n_stencil; /* vertices touched by flagged elements: stored stencils (0 on the finest level) */
 } agca_level_info_t;
 
 /* Human-readable name of a status code (static string). */
@@ -197,6 +203,26 @@ agca_status agca_load_vector(agca_ctx* ctx, const double* fbar_dev, double* b_de
  * AGCA_ENOTCONV if the tolerance was not met. */
 agca_status agca_solve(agca_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
                        int* iters, double* relres);
+
+/* The paper's outer solver (Sec. 4): flexible GMRES, restarted every
+ * `restart` iterations, right-preconditioned by the block-triangular
+ * preconditioner of Eq. 4.1 (z_p = -S~^-1 r_p, z_u = V-cycle(r_u - B^T z_p),
+ * the signs of K = [[A, B^T], [B, 0]] with B = -D), stopping when the
+ * residual norm of the Arnoldi process, then of the true FP64 residual, is
+ * at most rtol ||b|| (Eq. 4.3).  schur: 0 = S~^-1 the mean-free lumped 1/eta
+ * pressure mass; 1 = the diag(A)-BFBT of Eq. 4.2, S~^-1 = Z^-1 (B W^-1 A
+ * W^-1 B^T) Z^-1 with W = diag(A), Z = B W^-1 B^T applied matrix-free and
+ * Z^-1 by z_iters steps of Jacobi-preconditioned conjugate gradients on the
+ * mean-free pressures (diag(Z) probed with 27 colours at each call).
+ * work_dev: caller-owned device memory of agca_fgmres_workspace_size bytes
+ * (256-byte aligned; holds the 2 restart + 1 Krylov vectors).  x is
+ * overwritten (initial guess 0; pressure returned mean-free).  *iters,
+ * *relres (host): iterations and the final true relative residual.
+ * Synchronizes (once per iteration).  AGCA_ENOTCONV above the tolerance
+ * after maxit iterations. */
+agca_status agca_fgmres_workspace_size(const agca_ctx* ctx, int restart, size_t* bytes);
+agca_status agca_solve_fgmres(agca_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int restart,
+                              int schur, int z_iters, void* work_dev, size_t work_bytes, int* iters, double* relres);
 
 /* Element sensitivities g_e = -lambda_e^T (dA_e/dtheta_e) u_e for theta =
  * log(eta) (the viscous element matrix is linear in eta_e).  lam_u, u:

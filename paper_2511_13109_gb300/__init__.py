@@ -17,6 +17,8 @@ from .agca import (  # noqa: F401
     FIELD_MEAN,
     FIELD_MIN,
     FIELD_PMASS,
+    FIELD_SIDX,
+    FIELD_STENCIL,
     FP64,
     MIXED,
     PROJ_ARITHMETIC,

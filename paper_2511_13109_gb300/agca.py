@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libagca.so")
 FP64, MIXED = 0, 1
 F64, F32 = 0, 1
 PROJ_ARITHMETIC, PROJ_HARMONIC, PROJ_GEOMETRIC = 0, 1, 2
-FIELD_MEAN, FIELD_MAX, FIELD_MIN, FIELD_FLAGS, FIELD_LIST, FIELD_GCA, FIELD_DIAG, FIELD_COARSE, FIELD_PMASS = range(9)
+(FIELD_MEAN, FIELD_MAX, FIELD_MIN, FIELD_FLAGS, FIELD_LIST, FIELD_GCA, FIELD_DIAG, FIELD_COARSE, FIELD_PMASS,
+ FIELD_SIDX, FIELD_STENCIL) = range(11)
 
 STATUS = {0: "AGCA_OK", 1: "AGCA_EINVAL", 2: "AGCA_ENOMEM", 3: "AGCA_ECUDA", 4: "AGCA_ENOTCONV",
           5: "AGCA_ETIMEOUT", 6: "AGCA_EINTERNAL", 7: "AGCA_ESTATE"}
@@ -32,7 +33,7 @@ class AgcaError(RuntimeError):
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("vertices", ctypes.c_int64), ("elements", ctypes.c_int64),
-                ("n_flag", ctypes.c_int64), ("lambda_", ctypes.c_double)]
+                ("n_flag", ctypes.c_int64), ("lambda_", ctypes.c_double), ("n_stencil", ctypes.c_int64)]
 
 
 _lib = None
@@ -62,6 +63,8 @@ _SIGS = {
     "agca_precondition": ([_P, _P, _P], _I),
     "agca_load_vector": ([_P, _P, _P], _I),
     "agca_solve": ([_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "agca_fgmres_workspace_size": ([_P, _I, ctypes.POINTER(_SZ)], _I),
+    "agca_solve_fgmres": ([_P, _P, _P, _D, _I, _I, _I, _I, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "agca_element_sensitivity": ([_P, _P, _P, _P], _I),
     "agca_adjoint_gradient": ([_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I)], _I),
     "agca_stokes_apply_static": ([_I, _P, _P, _P, _P], _I),
@@ -335,6 +338,23 @@ class Context:
         self._check(st, "solve")
         return x, its.value, rel.value
 
+    def solve_fgmres(self, b: torch.Tensor, rtol: float = 1e-8, maxit: int = 5000, restart: int = 50,
+                     schur: str = "mass", z_iters: int = 30, x: torch.Tensor | None = None):
+        """The paper's outer solver: FGMRES with the block-triangular
+        preconditioner of Eq. 4.1 and S~^-1 = the lumped 1/eta mass ("mass")
+        or the diag(A)-BFBT of Eq. 4.2 ("bfbt"); see agca_solve_fgmres."""
+        _need(b, self.nt, torch.float64, "b")
+        x = torch.empty_like(b) if x is None else x
+        sz = _SZ()
+        self._check(lib().agca_fgmres_workspace_size(self._h, int(restart), ctypes.byref(sz)), "fgmres_workspace_size")
+        work = torch.empty(int(sz.value), dtype=torch.uint8, device=self.device)
+        its, rel = _I(), _D()
+        st = lib().agca_solve_fgmres(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), int(restart),
+                                     {"mass": 0, "bfbt": 1}[schur], int(z_iters), _ptr(work), sz.value,
+                                     ctypes.byref(its), ctypes.byref(rel))
+        self._check(st, "solve_fgmres")
+        return x, its.value, rel.value
+
     def element_sensitivity(self, lam_u: torch.Tensor, u: torch.Tensor):
         n = 3 * self.V[self.L]
         _need(lam_u, n, torch.float64, "lam_u")
@@ -395,7 +415,8 @@ class Context:
                  FIELD_FLAGS: (E, torch.uint8), FIELD_LIST: (info.n_flag, torch.int32),
                  FIELD_GCA: (info.n_flag * 144, torch.float64), FIELD_DIAG: (3 * V, torch.float64),
                  FIELD_COARSE: ((3 * (info.n - 1) ** 3) ** 2, torch.float64),
-                 FIELD_PMASS: (self.Vp, torch.float64)}[field]
+                 FIELD_PMASS: (self.Vp, torch.float64), FIELD_SIDX: (V, torch.int32),
+                 FIELD_STENCIL: (info.n_stencil * 135, torch.float64)}[field]
         out = torch.empty(max(1, shape[0]), dtype=shape[1], device=self.device)
         self._check(lib().agca_get_level_data(self._h, level, field, _ptr(out)), "get_level_data")
         return out[:shape[0]]

@@ -54,6 +54,31 @@ __host__ __device__ constexpr int corner_local(int t, int q) {
   return q == 0 ? 0 : q == 7 ? 3 : q == tet_corner(t, 1) ? 1 : q == tet_corner(t, 2) ? 2 : -1;
 }
 
+// The 15 Kuhn offsets of a vertex stencil (the vertex and the 14 neighbours it
+// shares an element edge with), in the order 0, +-e_x, +-e_y, +-e_z,
+// +-(e_x+e_y), +-(e_x+e_z), +-(e_y+e_z), +-(1,1,1): index of offset
+// (dx, dy, dz) (entries of one sign) and the offset of index o
+__host__ __device__ constexpr int kuhn_offset_index(int dx, int dy, int dz) {
+  return (dx | dy | dz) == 0 ? 0
+         : 1 + 2 * ((((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 1)   ? 0
+                    : (((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 2) ? 1
+                    : (((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 4) ? 2
+                    : (((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 3) ? 3
+                    : (((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 5) ? 4
+                    : (((dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)) == 6) ? 5
+                                                                          : 6) +
+               ((dx < 0 || dy < 0 || dz < 0) ? 1 : 0);
+}
+__host__ __device__ constexpr int kuhn_offset_comp(int o, int axis) {
+  // pattern of offset pair (o - 1) / 2: x, y, z, xy, xz, yz, xyz
+  return o == 0 ? 0
+                : (((((o - 1) >> 1) == 0 || ((o - 1) >> 1) == 3 || ((o - 1) >> 1) == 4 || ((o - 1) >> 1) == 6) && axis == 0) ||
+                   ((((o - 1) >> 1) == 1 || ((o - 1) >> 1) == 3 || ((o - 1) >> 1) == 5 || ((o - 1) >> 1) == 6) && axis == 1) ||
+                   ((((o - 1) >> 1) == 2 || ((o - 1) >> 1) == 4 || ((o - 1) >> 1) == 5 || ((o - 1) >> 1) == 6) && axis == 2))
+                      ? (((o - 1) & 1) ? -1 : 1)
+                      : 0;
+}
+
 // Refinement tables, built once on the host from the Kuhn ordering rule and
 // passed to kernels by value (kernel-parameter constant bank; see tables.cu):
 //  child[t][k] = {ox, oy, oz, t'}: k-th child (ascending fine element id) of a
@@ -79,7 +104,13 @@ struct LevelOp {
   const int32_t* list; // flagged element ids (coarse levels)
   int64_t n_flag;      // number of flagged elements
   T* ye;               // n_flag * 12 scratch: s_e A_e x_e of the flagged elements
-  const T* hedge;      // finest FP64 level: per-vertex edge sums of eta [3][V] (edge form), or nullptr
+  const T* hedge;      // FP64 levels: per-vertex edge sums of the DCA coefficient [3][V] (edge form), or nullptr
+  const T* coefm;      // FP64 coarse levels: DCA coefficient with flagged elements zeroed (edge form), or nullptr
+  // stored-Galerkin part as per-vertex stencils (Remark 5): stencil index of a
+  // vertex or -1, 15 x 3 x 3 couplings per touched vertex, FP32 scale (mixed)
+  const int32_t* sidx;
+  const T* sten;
+  const T* sscale;
 };
 
 __host__ __device__ inline int64_t nverts(int n) { return (int64_t)(n + 1) * (n + 1) * (n + 1); }
@@ -166,9 +197,10 @@ TileGrid stencil_tiles(int n, int by, int zch_req);
 // RESID and the Chebyshev steps, with op.hedge = the per-vertex sums of eta
 // over the 6 tetrahedra around each forward axis edge (launch_edge_sums)
 TileGrid edge_tiles(int n, int zch_req);
-cudaError_t launch_edge_sums(int n, const double* eta, double* hedge, cudaStream_t s);
-cudaError_t launch_stencil_edge(int mode, const LevelOp<double>& op, const StencilArgs<double>& a, cudaStream_t s,
-                                int zch_req);
+template <typename T>
+cudaError_t launch_edge_sums(int n, const T* eta, T* hedge, cudaStream_t s);
+template <typename T>
+cudaError_t launch_stencil_edge(int mode, const LevelOp<T>& op, const StencilArgs<T>& a, cudaStream_t s, int zch_req);
 
 // ------------------------------------------------------------ batched forms
 // One (problem, level) operator application inside a batched launch.
@@ -186,13 +218,15 @@ struct StencilTask {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s);
-// the edge form for a batch of FP64 finest-level tasks (tiles from edge_tiles)
-cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<double, double>* tasks, int ntasks, int64_t ntiles,
+// the edge form for a batch of tasks (tiles from edge_tiles)
+template <typename T>
+cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, int ntasks, int64_t ntiles,
                                       cudaStream_t s);
-// whether a batched step of this kind runs the edge form
+// whether a batched step of this kind runs the edge form: FP64 contexts keep
+// edge sums on every level, mixed ones on the finest level
 template <typename TS, typename T>
 constexpr bool edge_form_step(int mode, bool coarse) {
-  return sizeof(TS) == 8 && sizeof(T) == 8 && !coarse && mode != ST_STOKES;
+  return sizeof(TS) == sizeof(T) && mode != ST_STOKES && (sizeof(T) == 8 || !coarse);
 }
 
 // Element-wise batched tasks (transfers, conversions, coarsest solves).
@@ -247,6 +281,12 @@ template <typename T>
 cudaError_t launch_coarse_solve(int n, const double* linv_cm, const double* linv_rm, const T* r, T* z,
                                 cudaStream_t s);
 cudaError_t launch_pressure_mass(int np, const double* eta_f, double* pmass, double* pmass_inv, cudaStream_t s);
+// stencil storage of the flagged elements' Galerkin matrices (stencil_store.cu)
+cudaError_t launch_mark_vertices(int n, const uint8_t* flags, uint8_t* mark, cudaStream_t s);
+cudaError_t launch_stencil_assemble(int n, int64_t n_sv, const int32_t* slist, const int32_t* fidx, const double* gca,
+                                    double* sten, cudaStream_t s);
+cudaError_t launch_stencil_to_f32(int64_t n_sv, const double* s64, float* s32, float* scale, cudaStream_t s);
+cudaError_t launch_masked_coef(int64_t E, const double* mean, const int32_t* fidx, double* coefm, cudaStream_t s);
 cudaError_t launch_start_vector(int n, double* v, cudaStream_t s);
 
 // Stokes / Krylov kernels (krylov.cu)
@@ -256,7 +296,7 @@ enum MinresSlot {
   MS_INV_GAMMA_PREV, MS_UPD_SKIP, MS_DONE, MS_ITERS, MS_TOL_ABS, MS_DOT_KZZ, MS_DOT_ZV, MS_TMP0, MS_TMP1, MS_TMP2,
   MS_COUNT
 };
-enum VecOp { VOP_SUB = 0, VOP_ADD, VOP_COPY, VOP_ZERO, VOP_PDIV, VOP_SUBS, VOP_MUL, VOP_SCALE_RSQRT };
+enum VecOp { VOP_SUB = 0, VOP_ADD, VOP_COPY, VOP_ZERO, VOP_PDIV, VOP_SUBS, VOP_MUL, VOP_SCALE_RSQRT, VOP_RECIP };
 int dot_blocks();
 // out[j] = scale * sum_i xs[j][i] * ys[j][i] for npairs <= 3, deterministic
 cudaError_t launch_dots(int npairs, const double* const* xs, const double* const* ys, int64_t n, double* partials,
@@ -286,6 +326,19 @@ enum KBatchOp { KB_DOT = 0, KB_SUM, KB_LANCZOS, KB_UPDATE, KB_SCALARS, KB_PDIV, 
 cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t max_n, double* partials,
                                 cudaStream_t s);
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s);
+// FGMRES pieces: out[i] = w . V_i (i < nvec, V_i = V + i ld); w += sign sum_i coef[i] V_i;
+// y = a * s or a / s (s on the device); conjugate-gradient updates on device scalars
+// sc[0] = rho, sc[1] = p.q, sc[2] = rho_new; pressure-grid colouring for probing a diagonal
+cudaError_t launch_block_dot(int nvec, const double* V, int64_t ld, const double* w, int64_t n, double* partials,
+                             double* out, cudaStream_t s);
+cudaError_t launch_block_axpy(int nvec, const double* V, int64_t ld, const double* coef, double sign, double* w,
+                              int64_t n, cudaStream_t s);
+cudaError_t launch_scale(int64_t n, double* y, const double* a, const double* s_dev, bool recip, cudaStream_t s);
+cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* sc,
+                             cudaStream_t s);
+cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* sc, cudaStream_t s);
+cudaError_t launch_colour(int np, int colour, double* e, cudaStream_t s);
+cudaError_t launch_take_colour(int64_t n, const double* e, const double* y, double* d, cudaStream_t s);
 cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
                                cudaStream_t s);
 

@@ -34,7 +34,17 @@ struct Level {
   int32_t* list = nullptr;
   int64_t n_flag = 0;
   double* gca64 = nullptr;
-  double* hedge = nullptr;  // FP64 finest level: per-vertex edge sums of eta [3][V] (edge-form operator)
+  double* hedge = nullptr;  // FP64 contexts: per-vertex edge sums of the DCA coefficient [3][V] (edge form)
+  double* coefm = nullptr;  // FP64 coarse levels: DCA coefficient with flagged elements zeroed (edge form)
+  float* hedge32 = nullptr; // mixed contexts, finest level: FP32 edge sums of eta [3][V] (edge form)
+  // stencil storage of the flagged elements' Galerkin matrices (Remark 5)
+  uint8_t* vmark = nullptr;   // vertex touched by a flagged element
+  int32_t* sidx = nullptr;    // stencil index of a vertex or -1
+  int32_t* slist = nullptr;   // touched vertices, ascending
+  int64_t n_sv = 0;
+  double* sten64 = nullptr;   // n_sv * 135
+  float* sten32 = nullptr;    // mixed: S / s_v
+  float* sscale32 = nullptr;  // mixed: s_v
   double* diag = nullptr;
   double* invD64 = nullptr;
   // FP32 copies (mixed)
@@ -188,7 +198,14 @@ void carve_workspace(agca_ctx* ctx, char* base) {
       lv.mn = lv.mean;
     }
     if (mixed) lv.mean32 = cv.take<float>(lv.E);
-    if (!mixed && l == ctx->L) lv.hedge = cv.take<double>(3 * lv.V);
+    if (!mixed) lv.hedge = cv.take<double>(3 * lv.V);
+    if (mixed && l == ctx->L) lv.hedge32 = cv.take<float>(3 * lv.V);
+    if (!mixed && l < ctx->L) lv.coefm = cv.take<double>(lv.E);
+    if (l < ctx->L) {
+      lv.vmark = cv.take<uint8_t>(lv.V);
+      lv.sidx = cv.take<int32_t>(lv.V);
+      lv.slist = cv.take<int32_t>(lv.V);
+    }
     lv.diag = cv.take<double>(3 * lv.V);
     lv.invD64 = cv.take<double>(3 * lv.V);
     if (mixed) lv.invD32 = cv.take<float>(3 * lv.V);
@@ -199,7 +216,7 @@ void carve_workspace(agca_ctx* ctx, char* base) {
     lv.vr = cv.take<char>(3 * lv.V * (int64_t)es);
   }
   ctx->block_counts = cv.take<int32_t>(compact_scratch_blocks(max_coarse_e) + 1);
-  ctx->totals = cv.take<int64_t>(ctx->L + 1);
+  ctx->totals = cv.take<int64_t>(2 * (ctx->L + 1));  // flagged elements, then touched vertices, per level
   ctx->status = cv.take<int>(4);
   ctx->sc = cv.take<double>(64);
   ctx->partials = cv.take<double>(3 * (int64_t)dot_blocks());
@@ -223,10 +240,13 @@ void carve_gca(agca_ctx* ctx, char* base) {
     Level& lv = ctx->lev[l];
     lv.gca64 = cv.take<double>(std::max<int64_t>(1, lv.n_flag * 144));
     lv.ye64 = cv.take<double>(std::max<int64_t>(1, lv.n_flag * 12));
+    lv.sten64 = cv.take<double>(std::max<int64_t>(1, lv.n_sv * 135));
     if (mixed) {
       lv.ye32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag * 12));
       lv.gca32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag * 144));
       lv.gscale32 = cv.take<float>(std::max<int64_t>(1, lv.n_flag));
+      lv.sten32 = cv.take<float>(std::max<int64_t>(1, lv.n_sv * 135));
+      lv.sscale32 = cv.take<float>(std::max<int64_t>(1, lv.n_sv));
     }
   }
   ctx->gs_need = (cv.off + kAlign - 1) / kAlign * kAlign;
@@ -239,8 +259,11 @@ LevelOp<double> op64(const agca_ctx* ctx, int l) {
   op.h6 = 1.0 / (6.0 * lv.n);
   op.hq = 1.0 / (6.0 * (double)lv.n * lv.n);
   op.coef = lv.mean;
-  if (l == ctx->L) op.hedge = lv.hedge;
+  op.hedge = lv.hedge;
   if (l < ctx->L) {
+    op.coefm = lv.coefm;
+    op.sidx = lv.sidx;
+    op.sten = lv.n_sv > 0 ? lv.sten64 : nullptr;
     op.fidx = lv.fidx;
     op.gca = lv.gca64;
     op.list = lv.list;
@@ -257,7 +280,11 @@ LevelOp<float> op32(const agca_ctx* ctx, int l) {
   op.h6 = (float)(1.0 / (6.0 * lv.n));
   op.hq = (float)(1.0 / (6.0 * (double)lv.n * lv.n));
   op.coef = lv.mean32;
+  if (l == ctx->L) op.hedge = lv.hedge32;
   if (l < ctx->L) {
+    op.sidx = lv.sidx;
+    op.sten = lv.n_sv > 0 ? lv.sten32 : nullptr;
+    op.sscale = lv.n_sv > 0 ? lv.sscale32 : nullptr;
     op.fidx = lv.fidx;
     op.gca = lv.gca32;
     op.gscale = lv.gscale32;
@@ -685,6 +712,228 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
   return AGCA_OK;
 }
 
+// ------------------------------------------------------------------ FGMRES
+// The paper's outer solver (Sec. 4): flexible GMRES (restarted, right
+// preconditioning by a map that may vary between iterations), with the
+// block-triangular preconditioner of Eq. 4.1,
+//   z_p = -S~^-1 r_p,  z_u = A~^-1 (r_u - B^T z_p)
+// (the signs of K = [[A, B^T], [B, 0]] with B = -D, so that exact blocks give
+// K Q^-1 = [[I, 0], [B A^-1, I]]), A~^-1 one AGCA V-cycle and S~^-1 either
+// the mean-free lumped 1/eta pressure mass (the MINRES preconditioner's
+// pressure block) or the diag(A)-BFBT of Eq. 4.2,
+//   S~^-1 = Z^-1 (B W^-1 A W^-1 B^T) Z^-1,  W = diag(A),  Z = B W^-1 B^T,
+// with Z applied matrix-free (one Stokes apply of [W^-1 B^T t; 0] gives both
+// Z t and A W^-1 B^T t) and Z^-1 by Jacobi-preconditioned conjugate
+// gradients on the mean-free pressures (diag(Z) probed with 27 colours: Z
+// couples pressure vertices at most 2 cells apart).  Arnoldi by classical
+// Gram-Schmidt with one reorthogonalisation (two block dot products and two
+// block updates per iteration); the small Hessenberg least-squares problem
+// by Givens rotations on the host.
+struct FgmresWork {
+  double *V, *Z, *w, *t1, *t2, *partials, *hbuf, *ycoef, *zdinv, *cx, *cr, *cz, *cp, *cq, *m, *sc;
+  size_t need;
+};
+
+FgmresWork fgmres_layout(const agca_ctx* ctx, int restart, char* base) {
+  Carver cv(base);
+  const int64_t nt = ctx->nt, np = ctx->Vp;
+  FgmresWork w{};
+  w.V = cv.take<double>((int64_t)(restart + 1) * nt);
+  w.Z = cv.take<double>((int64_t)restart * nt);
+  w.w = cv.take<double>(nt);
+  w.t1 = cv.take<double>(nt);
+  w.t2 = cv.take<double>(nt);
+  w.partials = cv.take<double>((int64_t)(restart + 1) * dot_blocks());
+  w.hbuf = cv.take<double>(2 * (restart + 1) + 8);
+  w.ycoef = cv.take<double>(restart + 1);
+  w.zdinv = cv.take<double>(np);
+  w.cx = cv.take<double>(np);
+  w.cr = cv.take<double>(np);
+  w.cz = cv.take<double>(np);
+  w.cp = cv.take<double>(np);
+  w.cq = cv.take<double>(np);
+  w.m = cv.take<double>(np);
+  w.sc = cv.take<double>(8);
+  w.need = (cv.off + kAlign - 1) / kAlign * kAlign;
+  return w;
+}
+
+// t2 = K [W^-1 B^T p; 0]: pressure part Z p, velocity part A W^-1 B^T p (t1 scratch)
+agca_status z_apply(agca_ctx* ctx, const FgmresWork& W, const double* p) {
+  const int64_t n3 = 3 * ctx->lev[ctx->L].V, np = ctx->Vp;
+  cudaStream_t s = ctx->stream;
+  LK(1, launch_vec_op(VOP_ZERO, n3, W.t1, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_COPY, np, W.t1 + n3, p, nullptr, nullptr, nullptr, s));
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // t2_u = B^T p
+  LK(1, launch_vec_op(VOP_MUL, n3, W.t1, W.t2, ctx->lev[ctx->L].invD64, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_ZERO, np, W.t1 + n3, nullptr, nullptr, nullptr, nullptr, s));
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // [A W^-1 B^T p; Z p]
+  return AGCA_OK;
+}
+
+// y = y - mean(y) over the pressure DoFs
+agca_status mean_free(agca_ctx* ctx, double* y) {
+  const int64_t np = ctx->Vp;
+  LK(2, launch_sum(y, np, ctx->partials, ctx->sc + MS_TMP2, 1.0 / (double)np, ctx->stream));
+  LK(1, launch_vec_op(VOP_SUBS, np, y, y, nullptr, nullptr, ctx->sc + MS_TMP2, ctx->stream));
+  return AGCA_OK;
+}
+
+// x = Z^-1 rhs on the mean-free pressures: iters steps of Jacobi-preconditioned CG from 0
+agca_status z_solve(agca_ctx* ctx, const FgmresWork& W, const double* rhs, double* x, int iters) {
+  const int64_t np = ctx->Vp, n3 = 3 * ctx->lev[ctx->L].V;
+  cudaStream_t s = ctx->stream;
+  LK(1, launch_vec_op(VOP_COPY, np, W.cr, rhs, nullptr, nullptr, nullptr, s));
+  CKS(mean_free(ctx, W.cr));
+  LK(1, launch_vec_op(VOP_ZERO, np, x, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_MUL, np, W.cz, W.cr, W.zdinv, nullptr, nullptr, s));
+  CKS(mean_free(ctx, W.cz));
+  LK(1, launch_vec_op(VOP_COPY, np, W.cp, W.cz, nullptr, nullptr, nullptr, s));
+  CKS(dot1(ctx, W.cr, W.cz, np, W.sc + 0));
+  for (int it = 0; it < iters; ++it) {
+    CKS(z_apply(ctx, W, W.cp));
+    LK(1, launch_vec_op(VOP_COPY, np, W.cq, W.t2 + n3, nullptr, nullptr, nullptr, s));
+    CKS(dot1(ctx, W.cp, W.cq, np, W.sc + 1));
+    LK(1, launch_cg_update(np, x, W.cr, W.cp, W.cq, W.sc, s));
+    LK(1, launch_vec_op(VOP_MUL, np, W.cz, W.cr, W.zdinv, nullptr, nullptr, s));
+    CKS(mean_free(ctx, W.cz));
+    CKS(dot1(ctx, W.cr, W.cz, np, W.sc + 2));
+    LK(2, launch_cg_direction(np, W.cp, W.cz, W.sc, s));
+  }
+  CKS(mean_free(ctx, x));
+  return AGCA_OK;
+}
+
+// diag(Z) by probing with the 27 colours (i mod 3, j mod 3, k mod 3), inverted
+agca_status z_diag(agca_ctx* ctx, const FgmresWork& W) {
+  const int64_t np = ctx->Vp, n3 = 3 * ctx->lev[ctx->L].V;
+  cudaStream_t s = ctx->stream;
+  for (int c = 0; c < 27; ++c) {
+    LK(1, launch_colour(ctx->N, c, W.cp, s));
+    CKS(z_apply(ctx, W, W.cp));
+    LK(1, launch_take_colour(np, W.cp, W.t2 + n3, W.cq, s));
+  }
+  LK(1, launch_vec_op(VOP_RECIP, np, W.zdinv, W.cq, nullptr, nullptr, nullptr, s));
+  return AGCA_OK;
+}
+
+// z = Q^-1 r (Eq. 4.1); schur 0: lumped mass, 1: BFBT with z_iters CG steps per Z solve
+agca_status blocktri_precond(agca_ctx* ctx, const FgmresWork& W, const double* r, double* z, int schur, int z_iters) {
+  const int64_t n3 = 3 * ctx->lev[ctx->L].V, np = ctx->Vp;
+  cudaStream_t s = ctx->stream;
+  const double* rp = r + n3;
+  double* zp = z + n3;
+  if (schur == 0) {
+    const double inv = 1.0 / (double)np;
+    LK(2, launch_sum(rp, np, ctx->partials, ctx->sc + MS_TMP0, inv, s));
+    LK(1, launch_vec_op(VOP_PDIV, np, zp, rp, ctx->pmass_inv, nullptr, ctx->sc + MS_TMP0, s));
+    CKS(mean_free(ctx, zp));
+  } else {
+    CKS(z_solve(ctx, W, rp, W.m, z_iters));                 // t = Z^-1 r_p
+    CKS(z_apply(ctx, W, W.m));                              // t2_u = A W^-1 B^T t
+    LK(1, launch_vec_op(VOP_MUL, n3, W.t1, W.t2, ctx->lev[ctx->L].invD64, nullptr, nullptr, s));
+    LK(1, launch_vec_op(VOP_ZERO, np, W.t1 + n3, nullptr, nullptr, nullptr, nullptr, s));
+    CKS(stokes_dispatch(ctx, W.t1, W.t2, false));          // t2_p = B W^-1 A W^-1 B^T t
+    LK(1, launch_vec_op(VOP_COPY, np, W.m, W.t2 + n3, nullptr, nullptr, nullptr, s));
+    CKS(z_solve(ctx, W, W.m, zp, z_iters));                 // S~^-1 r_p
+  }
+  // z_p = -S~^-1 r_p
+  LK(1, launch_vec_op(VOP_ZERO, np, W.cq, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_SUB, np, zp, W.cq, zp, nullptr, nullptr, s));
+  // z_u = A~^-1 (r_u - B^T z_p)
+  LK(1, launch_vec_op(VOP_ZERO, n3, W.t1, nullptr, nullptr, nullptr, nullptr, s));
+  LK(1, launch_vec_op(VOP_COPY, np, W.t1 + n3, zp, nullptr, nullptr, nullptr, s));
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // t2_u = B^T z_p
+  LK(1, launch_vec_op(VOP_SUB, n3, W.t1, r, W.t2, nullptr, nullptr, s));
+  CKS(vcycle_impl(ctx, W.t1, z));
+  return AGCA_OK;
+}
+
+agca_status fgmres_impl(agca_ctx* ctx, const FgmresWork& W, int restart, const double* b_in, double* x, double rtol,
+                        int maxit, int schur, int z_iters, int* iters, double* relres) {
+  const int64_t nt = ctx->nt;
+  cudaStream_t s = ctx->stream;
+  double* r = ctx->kv[KV_R];
+  double* kx = ctx->kv[KV_KZ];
+  double* bm = ctx->kv[KV_B];
+  LK(1, launch_vec_op(VOP_COPY, nt, bm, b_in, nullptr, nullptr, nullptr, s));
+  LK(1, launch_mask_boundary(ctx->lev[ctx->L].n, bm, s));
+  LK(1, launch_vec_op(VOP_ZERO, nt, x, nullptr, nullptr, nullptr, nullptr, s));
+  if (schur == 1) CKS(z_diag(ctx, W));
+  double nb2 = 0.0;
+  CKS(dot1(ctx, bm, bm, nt, ctx->sc + MS_TMP0));
+  CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nb2));
+  const double nb = sqrt(nb2);
+  int its = 0;
+  double rel = nb > 0.0 ? 1.0 : 0.0;
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart),
+      hv(2 * (restart + 1) + 1);
+  auto Hh = [&](int i, int j) -> double& { return H[(size_t)i * restart + j]; };
+  double* const hdev = W.hbuf;                     // [0, restart+1): first pass, then second pass, then |w|^2
+  double* const h2dev = W.hbuf + (restart + 1);
+  double* const wn2 = W.hbuf + 2 * (restart + 1);
+  while (nb > 0.0) {
+    CKS(stokes_dispatch(ctx, x, kx, false));
+    LK(1, launch_vec_op(VOP_SUB, nt, r, bm, kx, nullptr, nullptr, s));
+    double beta2 = 0.0;
+    CKS(dot1(ctx, r, r, nt, ctx->sc + MS_TMP0));
+    CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &beta2));
+    const double beta = sqrt(beta2);
+    rel = beta / nb;
+    if (!(rel > rtol) || its >= maxit) break;
+    LK(1, launch_vec_op(VOP_SCALE_RSQRT, nt, W.V, r, nullptr, nullptr, ctx->sc + MS_TMP0, s));  // v0 = r / beta
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int m = 0;
+    for (int j = 0; j < restart; ++j) {
+      double* vj = W.V + (int64_t)j * nt;
+      double* zj = W.Z + (int64_t)j * nt;
+      CKS(blocktri_precond(ctx, W, vj, zj, schur, z_iters));
+      CKS(stokes_dispatch(ctx, zj, W.w, false));
+      // classical Gram-Schmidt, twice
+      LK(2, launch_block_dot(j + 1, W.V, nt, W.w, nt, W.partials, hdev, s));
+      LK(1, launch_block_axpy(j + 1, W.V, nt, hdev, -1.0, W.w, nt, s));
+      LK(2, launch_block_dot(j + 1, W.V, nt, W.w, nt, W.partials, h2dev, s));
+      LK(1, launch_block_axpy(j + 1, W.V, nt, h2dev, -1.0, W.w, nt, s));
+      CKS(dot1(ctx, W.w, W.w, nt, wn2));
+      LK(1, launch_vec_op(VOP_SCALE_RSQRT, nt, W.V + (int64_t)(j + 1) * nt, W.w, nullptr, nullptr, wn2, s));
+      CK(cudaMemcpyAsync(hv.data(), W.hbuf, (2 * (restart + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) Hh(i, j) = hv[i] + hv[restart + 1 + i];
+      const double hn = sqrt(std::max(hv[2 * (restart + 1)], 0.0));
+      // previous rotations, then the one that annihilates H(j+1, j)
+      for (int i = 0; i < j; ++i) {
+        const double a = Hh(i, j), b = Hh(i + 1, j);
+        Hh(i, j) = cs[i] * a + sn[i] * b;
+        Hh(i + 1, j) = -sn[i] * a + cs[i] * b;
+      }
+      const double a = Hh(j, j);
+      const double den = sqrt(a * a + hn * hn);
+      cs[j] = den > 0.0 ? a / den : 1.0;
+      sn[j] = den > 0.0 ? hn / den : 0.0;
+      Hh(j, j) = den;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      m = j + 1;
+      if (std::fabs(g[j + 1]) <= rtol * nb || its >= maxit || hn == 0.0) break;
+    }
+    // x += Z y with R y = g (back substitution)
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < m; ++k) acc -= Hh(i, k) * y[k];
+      y[i] = Hh(i, i) != 0.0 ? acc / Hh(i, i) : 0.0;
+    }
+    CK(cudaMemcpyAsync(W.ycoef, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    LK(1, launch_block_axpy(m, W.Z, nt, W.ycoef, 1.0, x, nt, s));
+    CKS(project_pressure(ctx, x));
+  }
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  if (!(rel <= rtol)) return ctx->fail(AGCA_ENOTCONV, "FGMRES stopped above the tolerance");
+  return AGCA_OK;
+}
+
 agca_status check_status(agca_ctx* ctx, const char* where) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -920,7 +1169,7 @@ void push_stencil(agca_batch* b, std::vector<BatchStep>& steps, int mode, bool c
     tk.tg = edge_form_step<TS, T>(mode, coarse) ? edge_tiles(tk.op.n, zch) : stencil_tiles(tk.op.n, 8, zch);
     tk.tile0 = tiles;
     tiles += (int64_t)tk.tg.per_z() * tk.tg.gz;
-    gca = std::max<int64_t>(gca, tk.op.n_flag * 12);
+    gca = std::max<int64_t>(gca, tk.op.sten ? 0 : tk.op.n_flag * 12);  // stencils need no product launch
   }
   BatchStep st{0, mode, prec, coarse, push_tasks(b, t), (int)t.size(), tiles, coarse ? gca : 0, 0};
   steps.push_back(st);
@@ -1350,11 +1599,17 @@ agca_status flag_impl(agca_ctx* ctx, double nu, const double* eta_v, size_t* gca
   for (int l = 1; l < L; ++l) {
     Level& lc = ctx->lev[l];
     LK(3, launch_compact(lc.flags, lc.E, lc.fidx, lc.list, ctx->block_counts, ctx->totals + l, s));
+    // vertices of flagged elements: the stencil store (Remark 5)
+    LK(1, launch_mark_vertices(lc.n, lc.flags, lc.vmark, s));
+    LK(3, launch_compact(lc.vmark, lc.V, lc.sidx, lc.slist, ctx->block_counts, ctx->totals + (L + 1) + l, s));
   }
-  std::vector<int64_t> tot(L + 1, 0);
-  CK(cudaMemcpyAsync(tot.data(), ctx->totals, (L + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  std::vector<int64_t> tot(2 * (L + 1), 0);
+  CK(cudaMemcpyAsync(tot.data(), ctx->totals, 2 * (L + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  for (int l = 1; l < L; ++l) ctx->lev[l].n_flag = tot[l];
+  for (int l = 1; l < L; ++l) {
+    ctx->lev[l].n_flag = tot[l];
+    ctx->lev[l].n_sv = tot[L + 1 + l];
+  }
   carve_gca(ctx, nullptr);
   *gca_bytes = ctx->gs_need;
   ctx->flagged = true;
@@ -1415,6 +1670,18 @@ agca_status agca_setup(agca_ctx* ctx) {
     LK(1, launch_galerkin(lc.n, lc.n_flag, lc.list, lf.n, child_finest, lf.mean, child_finest ? nullptr : lf.fidx,
                        child_finest ? nullptr : lf.gca64, lc.gca64, s));
   }
+  // stencil storage of the stored-Galerkin part (Remark 5) and, in FP64, the
+  // edge-form data of the coarse DCA part (flagged elements masked)
+  for (int l = 1; l < L; ++l) {
+    Level& lc = ctx->lev[l];
+    LK(1, launch_stencil_assemble(lc.n, lc.n_sv, lc.slist, lc.fidx, lc.gca64, lc.sten64, s));
+    if (mixed) {
+      LK(1, launch_stencil_to_f32(lc.n_sv, lc.sten64, lc.sten32, lc.sscale32, s));
+    } else {
+      LK(1, launch_masked_coef(lc.E, lc.mean, lc.fidx, lc.coefm, s));
+      LK(1, launch_edge_sums(lc.n, lc.coefm, lc.hedge, s));
+    }
+  }
   for (int l = 1; l <= L; ++l) {
     Level& lv = ctx->lev[l];
     if (mixed) {
@@ -1423,6 +1690,7 @@ agca_status agca_setup(agca_ctx* ctx) {
     }
     LK(1, launch_diag(op64(ctx, l), lv.diag, lv.invD64, mixed ? lv.invD32 : nullptr, s));
   }
+  if (mixed) LK(1, launch_edge_sums<float>(ctx->lev[L].n, ctx->lev[L].mean32, ctx->lev[L].hedge32, s));
   // coarsest operator: dense assembly, Cholesky, explicit inverse factor
   LK(1, launch_coarse_assemble(op64(ctx, 1), ctx->cdense, s));
   CK(cudaMemcpyAsync(ctx->cfac, ctx->cdense, (size_t)ctx->mc * ctx->mc * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1512,6 +1780,24 @@ agca_status agca_solve(agca_ctx* ctx, const double* b_dev, double* x_dev, double
   if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
   if (!(rtol > 0.0) || maxit < 1) return ctx->fail(AGCA_EINVAL, "rtol must be > 0 and maxit >= 1");
   return solve_impl(ctx, b_dev, x_dev, rtol, maxit, iters, relres);
+}
+
+agca_status agca_fgmres_workspace_size(const agca_ctx* ctx, int restart, size_t* bytes) {
+  if (!ctx || !bytes || restart < 1 || restart > 500) return AGCA_EINVAL;
+  *bytes = fgmres_layout(ctx, restart, nullptr).need;
+  return AGCA_OK;
+}
+
+agca_status agca_solve_fgmres(agca_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int restart,
+                              int schur, int z_iters, void* work_dev, size_t work_bytes, int* iters, double* relres) {
+  if (!ctx || !b_dev || !x_dev || !work_dev) return AGCA_EINVAL;
+  if (restart < 1 || restart > 500 || maxit < 1 || !(rtol > 0.0) || (schur != 0 && schur != 1) || z_iters < 0)
+    return ctx->fail(AGCA_EINVAL, "bad FGMRES parameters");
+  if (!ctx->setup_done) return ctx->fail(AGCA_ESTATE, "setup first");
+  if (((uintptr_t)work_dev % kAlign) != 0) return ctx->fail(AGCA_EINVAL, "workspace must be 256-byte aligned");
+  const FgmresWork W = fgmres_layout(ctx, restart, static_cast<char*>(work_dev));
+  if (work_bytes < W.need) return ctx->fail(AGCA_ENOMEM, "FGMRES workspace too small");
+  return fgmres_impl(ctx, W, restart, b_dev, x_dev, rtol, maxit, schur, z_iters, iters, relres);
 }
 
 agca_status agca_element_sensitivity(agca_ctx* ctx, const double* lam_u_dev, const double* u_dev, double* g_dev) {
@@ -1649,6 +1935,7 @@ agca_status agca_level_info(agca_ctx* ctx, int level, agca_level_info_t* out) {
   out->vertices = lv.V;
   out->elements = lv.E;
   out->n_flag = level < ctx->L ? lv.n_flag : 0;
+  out->n_stencil = level < ctx->L ? lv.n_sv : 0;
   out->lambda = lv.lambda;
   return AGCA_OK;
 }
@@ -1682,6 +1969,12 @@ agca_status agca_get_level_data(agca_ctx* ctx, int level, int field, void* dst_d
     case AGCA_FIELD_PMASS:
       if (level != ctx->L - 1 || !ctx->setup_done) return ctx->fail(AGCA_ESTATE, "pressure mass: level L-1 after setup");
       src = ctx->pmass; bytes = ctx->Vp * sizeof(double); break;
+    case AGCA_FIELD_SIDX:
+      if (!coarse || !ctx->flagged) return ctx->fail(AGCA_ESTATE, "stencil indices: coarse level after agca_flag");
+      src = lv.sidx; bytes = lv.V * sizeof(int32_t); break;
+    case AGCA_FIELD_STENCIL:
+      if (!coarse || !ctx->setup_done) return ctx->fail(AGCA_ESTATE, "stencils: coarse level after setup");
+      src = lv.sten64; bytes = lv.n_sv * 135 * sizeof(double); break;
     default: return ctx->fail(AGCA_EINVAL, "unknown field");
   }
   if (bytes) CK(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -150,6 +150,34 @@ __device__ __forceinline__ void gca_row(const LevelOp<T>& op, const StencilArgs<
   });
 }
 
+// Stored-Galerkin part of a coarse operator at interior vertex (i, j, k) of a
+// grid with n cubes per axis (Remark 5): g += sum_o S[o] x(v + o) over the 15
+// Kuhn offsets, S = op.sten + 135 s for the vertex's stencil index s; Dirichlet
+// neighbours contribute nothing.  xval(d, v'): operator input (component d,
+// vertex v').  Fixed order: offset, then component.
+template <typename T, typename XF>
+__device__ __forceinline__ void stencil_gather(const LevelOp<T>& op, const int s, const int i, const int j, const int k,
+                                               XF xval, T (&g)[3]) {
+  const int n = op.n, nv = n + 1;
+  const T* S = op.sten + (int64_t)s * 135;
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int o = 0; o < 15; ++o) {
+    const int a = i + kuhn_offset_comp(o, 0), b = j + kuhn_offset_comp(o, 1), c = k + kuhn_offset_comp(o, 2);
+    if (a <= 0 || b <= 0 || c <= 0 || a >= n || b >= n || c >= n) continue;
+    const int w = a + nv * (b + nv * c);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T xv = (T)xval(d, w);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) acc[r] = fma(S[o * 9 + r * 3 + d], xv, acc[r]);
+    }
+  }
+  const T sc = op.sscale ? op.sscale[s] : T(1);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) g[r] = op.sscale ? sc * acc[r] : acc[r];
+}
+
 // Result of a fused stencil mode at one vertex from the operator value y =
 // (A x)_v, the vertex's own iterate xo, rhs eb, inverse diagonal ed and
 // previous iterate ep (Chebyshev steps of Sec. 4; CHEB_PRE starts from x0 = 0

@@ -179,6 +179,7 @@ __global__ void vec_op_kernel(int op, int64_t n, double* y, const double* a, con
       case VOP_SUBS: y[i] = a[i] - s0; break;             // y = a - s
       case VOP_MUL: y[i] = a[i] * b[i]; break;            // y = a * b
       case VOP_SCALE_RSQRT: y[i] = a[i] * (1.0 / sqrt(s0)); break;  // y = a / sqrt(s)
+      case VOP_RECIP: y[i] = a[i] > 0.0 ? 1.0 / a[i] : 0.0; break;  // y = 1 / a (0 where a <= 0)
       default: break;
     }
   }
@@ -269,6 +270,96 @@ __global__ void mask_boundary_kernel(int n, double* x) {
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ----------------------------------------------------------- FGMRES pieces
+// Gram-Schmidt against a block of vectors V_i = V + i * ld (i < nvec): per
+// block and vector the partial sums of w . V_i over the block's grid-stride
+// range, in a fixed order (deterministic); the final sums by reduce_final_kernel
+__global__ void __launch_bounds__(kRedThreads) block_dot_kernel(int nvec, const double* __restrict__ V, int64_t ld,
+                                                                const double* __restrict__ w, int64_t n,
+                                                                double* __restrict__ partials) {
+  grid_dep_entry();
+  __shared__ double red[kRedThreads / 32];
+  for (int i = 0; i < nvec; ++i) {
+    const double* vi = V + i * ld;
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+      acc = fma(w[q], vi[q], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0.0;
+      for (int k = 0; k < kRedThreads / 32; ++k) v += red[k];
+      partials[(int64_t)i * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// w += sign * sum_i coef[i] V_i (coefficients on the device), summed in i order
+__global__ void __launch_bounds__(kRedThreads) block_axpy_kernel(int nvec, const double* __restrict__ V, int64_t ld,
+                                                                 const double* __restrict__ coef, double sign,
+                                                                 double* __restrict__ w, int64_t n) {
+  grid_dep_entry();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nvec; ++i) acc = fma(coef[i], V[i * ld + q], acc);
+    w[q] = fma(sign, acc, w[q]);
+  }
+}
+
+// y = a * s (s on the device)
+__global__ void scale_kernel(int64_t n, double* __restrict__ y, const double* __restrict__ a,
+                             const double* __restrict__ s, int recip) {
+  grid_dep_entry();
+  const double f = recip ? 1.0 / s[0] : s[0];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = a[q] * f;
+}
+
+// conjugate-gradient vector updates on the device scalars sc: x += alpha p,
+// r -= alpha q with alpha = sc[0] / sc[1]; p = z + beta p with beta = sc[2] / sc[0]
+__global__ void cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                 const double* __restrict__ p, const double* __restrict__ q,
+                                 const double* __restrict__ sc) {
+  grid_dep_entry();
+  const double alpha = sc[1] != 0.0 ? sc[0] / sc[1] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+__global__ void cg_direction_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                                    double* __restrict__ sc) {
+  grid_dep_entry();
+  const double beta = sc[0] != 0.0 ? sc[2] / sc[0] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+__global__ void cg_shift_kernel(double* sc) {
+  grid_dep_entry();
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = sc[2];  // rho <- rho_new
+}
+
+// indicator of the pressure vertices (i, j, k) with (i mod 3, j mod 3, k mod 3) = colour
+__global__ void colour_kernel(int np, int colour, double* __restrict__ e) {
+  grid_dep_entry();
+  const int nv = np + 1;
+  const int64_t V = (int64_t)nv * nv * nv;
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  e[v] = (i % 3) + 3 * (j % 3) + 9 * (k % 3) == colour ? 1.0 : 0.0;
+}
+// d[v] = y[v] where e[v] = 1 (the colour's diagonal entries of the probed operator)
+__global__ void take_colour_kernel(int64_t n, const double* __restrict__ e, const double* __restrict__ y,
+                                   double* __restrict__ d) {
+  grid_dep_entry();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (e[i] != 0.0) d[i] = y[i];
+}
+
 }  // namespace
 
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s) {
@@ -309,6 +400,46 @@ cudaError_t launch_vec_op(int op, int64_t n, double* y, const double* a, const d
 
 cudaError_t launch_minres_init(double* sc, double tol_rel, cudaStream_t s) {
   KL(launch_k(minres_init_kernel, dim3(1), dim3(32), 0, s, sc, tol_rel));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_dot(int nvec, const double* V, int64_t ld, const double* w, int64_t n, double* partials,
+                             double* out, cudaStream_t s) {
+  KL(launch_k(block_dot_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, nvec, V, ld, w, n, partials));
+  KL(launch_k(reduce_final_kernel, dim3(1), dim3(256), 0, s, (const double*)partials, kRedBlocks, nvec, out, 1.0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_axpy(int nvec, const double* V, int64_t ld, const double* coef, double sign, double* w,
+                              int64_t n, cudaStream_t s) {
+  KL(launch_k(block_axpy_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, nvec, V, ld, coef, sign, w, n));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(int64_t n, double* y, const double* a, const double* s_dev, bool recip, cudaStream_t s) {
+  KL(launch_k(scale_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, y, a, s_dev, recip ? 1 : 0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* sc,
+                             cudaStream_t s) {
+  KL(launch_k(cg_update_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, x, r, p, q, sc));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* sc, cudaStream_t s) {
+  KL(launch_k(cg_direction_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, p, z, sc));
+  KL(launch_k(cg_shift_kernel, dim3(1), dim3(32), 0, s, sc));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colour(int np, int colour, double* e, cudaStream_t s) {
+  KL(launch_k(colour_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, np, colour, e));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_take_colour(int64_t n, const double* e, const double* y, double* d, cudaStream_t s) {
+  KL(launch_k(take_colour_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, e, y, d));
   return cudaGetLastError();
 }
 

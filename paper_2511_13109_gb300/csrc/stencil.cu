@@ -19,6 +19,7 @@
 //   + [(Y(i-1,j-1,k)[3] + Y(i,j-1,k)[2]) + (Y(i-1,j,k)[1] + Y(i,j,k)[0])]
 // whatever the tile shape (results do not depend on it).
 #include <algorithm>
+#include <type_traits>
 
 #include "agca_internal.cuh"
 #include "device_ops.cuh"
@@ -354,7 +355,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
         cube_dca<T, NC>(Xl, Xh, cf, Y);
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
-          if (f[t] >= 0) {  // stored Galerkin element: s_e A_e x_e precomputed by gca_apply_kernel
+          if (f[t] >= 0 && !op.sten) {  // stored Galerkin element: s_e A_e x_e precomputed by gca_apply_kernel
             const T* yv = op.ye + f[t] * 12;
 #pragma unroll
             for (int r = 0; r < 12; ++r) {
@@ -414,6 +415,21 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
       for (int c = 0; c < NC; ++c) {
         yk[c] = acc[c] + (s1[0][c] + up[0][c]);
         acc[c] = s1[1][c] + up[1][c];
+      }
+      if constexpr (COARSE) {
+        // stored-Galerkin part of the touched vertices (stencil storage)
+        if (op.sten && inner) {
+          const int sv = op.sidx[vo];
+          if (sv >= 0) {
+            T g[3];
+            stencil_gather<T>(op, sv, vx, vy, k, [&](int d, int w) -> TS {
+              if (MODE == ST_CHEB_PRE) return a.s2 * __ldg(a.invD + d * V + w) * __ldg(a.b + d * V + w);
+              return __ldg(a.x + d * V + w);
+            }, g);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) yk[c] += g[c];
+          }
+        }
       }
       if (out_k) {
 #pragma unroll
@@ -545,7 +561,7 @@ __global__ void gca_apply_batch_kernel(const StencilTask<TS, T>* __restrict__ ta
 template <typename TS, typename T, int BY, bool COARSE>
 cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s, int zch_req) {
   const TileGrid tg = stencil_tiles(op.n, BY, zch_req);
-  if (COARSE && op.n_flag > 0) {
+  if (COARSE && op.n_flag > 0 && !op.sten) {
     const unsigned gb = (unsigned)((op.n_flag * 12 + 127) / 128);
     if (mode == ST_CHEB_PRE)
       KL(launch_k(gca_apply_kernel<TS, T, true>, dim3(gb), dim3(128), 0, s, op, a));
@@ -675,10 +691,8 @@ TileGrid stencil_tiles(int n, int BY, int zch_req) {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s) {
-  if constexpr (sizeof(TS) == 8 && sizeof(T) == 8) {
-    if (edge_form_step<TS, T>(mode, coarse))
-      return launch_stencil_edge_batch(mode, reinterpret_cast<const StencilTask<double, double>*>(tasks), ntasks,
-                                       ntiles, s);
+  if constexpr (std::is_same<TS, T>::value) {
+    if (edge_form_step<TS, T>(mode, coarse)) return launch_stencil_edge_batch<T>(mode, tasks, ntasks, ntiles, s);
   }
   if (coarse) return launch_batch_mode<TS, T, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
   return launch_batch_mode<TS, T, 8, false>(mode, tasks, ntasks, ntiles, 0, s);
@@ -694,11 +708,9 @@ template <typename TS, typename T>
 cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a, cudaStream_t s,
                            const TileCfg* cfg) {
   const int by = cfg ? cfg->by : 8, zch = cfg ? cfg->zch : 0;
-  if constexpr (sizeof(T) == 8 && sizeof(TS) == 8) {
-    // the FP64 finest level runs the edge form when its edge sums exist
-    if (!op.fidx && op.hedge && mode != ST_STOKES)
-      return launch_stencil_edge(mode, reinterpret_cast<const LevelOp<double>&>(op),
-                                 reinterpret_cast<const StencilArgs<double>&>(a), s, zch);
+  if constexpr (std::is_same<TS, T>::value) {
+    // levels with edge sums (FP64: every level; FP32: the finest) run the edge form
+    if (op.hedge && mode != ST_STOKES && (sizeof(T) == 8 || !op.fidx)) return launch_stencil_edge<T>(mode, op, a, s, zch);
   }
   if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
     if (by == 12) {

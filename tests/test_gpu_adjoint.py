@@ -104,16 +104,17 @@ def test_adjoint_full_size_finite_differences(prec):
     """The adjoint benchmark workload (64^3 pressure cubes, 8 spheres, jump
     1e4, observation from log-viscosity + N(0, 0.1^2)): the autograd gradient
     against central finite differences of the forward solve along seeded
-    directions, to 1e-5 relative.  Forward and adjoint solves go to a 1e-11
-    relative residual, so their errors enter the central difference with
-    eps = 1e-4 well below 1e-5 of it."""
+    directions, to 1e-5 relative.  Forward and adjoint solves go to a 1e-10
+    relative residual (the FP64 floor of this field at 64^3 is 4.4e-11) and
+    the central difference takes eps = 1e-3: the solves' errors then enter
+    the difference at about 1e-7 of it and the truncation at about 1e-6."""
     from synth import adjoint_problem
 
     N = 64
     p, theta_obs = adjoint_problem(N)
     fbar = torch.from_numpy(p.fbar.ravel()).to(DEV)
     precision = pkg.MIXED if prec == "mixed" else pkg.FP64
-    prob = pkg.StokesProblem(N, fbar, precision=precision, rtol=1e-11, maxit=60000, device=DEV)
+    prob = pkg.StokesProblem(N, fbar, precision=precision, rtol=1e-10, maxit=60000, device=DEV)
     theta = torch.log(torch.from_numpy(p.eta).to(DEV))
     with torch.no_grad():
         u_obs = pkg.stokes_velocity(torch.from_numpy(theta_obs).to(DEV), prob).clone()
@@ -128,7 +129,7 @@ def test_adjoint_full_size_finite_differences(prec):
     (0.5 * torch.sum((u - u_obs) ** 2)).backward()
     g = th.grad.clone()
     assert torch.isfinite(g).all()
-    eps = 1e-4
+    eps = 1e-3
     worst = 0.0
     for k in range(FULL_DIRECTIONS[prec]):
         d = torch.from_numpy(np.random.default_rng(200 + k).normal(size=theta.numel())).to(DEV)

@@ -1,12 +1,18 @@
 """Solution error, not only the residual, at full size.
 
-A 1e-8 relative residual does not bound the solution error by 1e-8 when the
-viscosity jumps by 1e6, so solution parity is checked with both sides solved
-to a 1e-11 relative residual on the true FP64 operator:
-  * 64^3 pressure cubes, 8 spheres, jump 1e6 (the 6.4 M-DoF workload): the
-    mixed-precision solve and the batched solve against the FP64 GPU solve;
-  * 32^3 pressure cubes: the FP64 and mixed GPU solves against the oracle's
-    own MINRES with residual refinement (no code shared with the GPU path).
+A relative residual does not bound the solution error by the same factor
+when the viscosity jumps by orders of magnitude, so solution parity is
+checked with both sides solved well below the timed 1e-8.  The attainable
+true residual of an FP64 Stokes solve is limited by the rounding of K x
+itself, about eps * ||K|| ||x|| / ||b||: measured on 64^3 pressure cubes it
+is 4.4e-11 for 8 spheres with jump 1e4 and 2.2e-9 with jump 1e6.  Hence:
+  * 64^3, 8 spheres, jump 1e4 (the adjoint workload's field): the mixed and
+    the batched solves against the FP64 GPU solve, all to 1e-10;
+  * 64^3, 8 spheres, jump 1e6 (the 6.4 M-DoF workload): FP64 and mixed
+    solves to 5e-9, just above the floor; their difference is stated;
+  * 32^3 pressure cubes, jump 1e2: the FP64 and mixed GPU solves against
+    the oracle's own MINRES with residual refinement (no code shared with
+    the GPU path), all to 1e-11.
 The error of the timed solves (residual 1e-8) against the same reference is
 printed beside them.
 """
@@ -27,18 +33,23 @@ def _rel(x, ref):
     return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
 
 
+REF64 = 1e-10
+
+
 @pytest.fixture(scope="module")
 def ref64():
+    from synth import adjoint_problem
+
     N = 64
-    p = sphere_sinkers(N, 8, 0.08, 0.01, 1e6, device=DEV)
+    p, _ = adjoint_problem(N, device=DEV)   # 8 spheres, jump 1e4
     L = pkg.default_levels(N)
     eta = torch.from_numpy(p.eta).to(DEV)
     fbar = torch.from_numpy(p.fbar.ravel()).to(DEV)
     c = pkg.Context(N, L, pkg.FP64, device=DEV)
     c.prepare(eta, 10.0)
     b = c.load_vector(fbar)
-    x, its, rel = c.solve(b, TIGHT, 40000)
-    assert rel <= TIGHT
+    x, its, rel = c.solve(b, REF64, 40000)
+    assert rel <= REF64
     del c
     return N, L, eta, fbar, b, x
 
@@ -47,15 +58,15 @@ def test_mixed_solution_error_full_size(ref64):
     N, L, eta, fbar, b, x64 = ref64
     c = pkg.Context(N, L, pkg.MIXED, device=DEV)
     c.prepare(eta, 10.0)
-    x, its, rel = c.solve(b, TIGHT, 40000)
-    assert rel <= TIGHT
+    x, its, rel = c.solve(b, REF64, 40000)
+    assert rel <= REF64
     err = _rel(x, x64)
     x8, its8, rel8 = c.solve(b, 1e-8, 40000)
     err8 = _rel(x8, x64)
-    print(f"\n64^3 mixed vs FP64 solution: {err:.2e} (both to 1e-11, {its} iterations); "
+    print(f"\n64^3 jump 1e4: mixed vs FP64 solution {err:.2e} (both to 1e-10, {its} iterations); "
           f"timed tolerance 1e-8: {err8:.2e} ({its8} iterations)")
     assert err <= 1e-8
-    assert err8 <= 1e-4
+    assert err8 <= 1e-5
 
 
 def test_batched_solution_error_full_size(ref64):
@@ -66,11 +77,33 @@ def test_batched_solution_error_full_size(ref64):
     B = pkg.Batch([N, 32], pkg.MIXED, device=DEV)
     B.prepare([eta, eta2], 10.0)
     b2 = B.load_vector(1, torch.from_numpy(q.fbar.ravel()).to(DEV))
-    xs, its, rel = B.solve([b, b2], TIGHT, 40000)
-    assert max(rel) <= TIGHT
+    xs, its, rel = B.solve([b, b2], REF64, 40000)
+    assert max(rel) <= REF64
     err = _rel(xs[0], x64)
-    print(f"\n64^3 batched vs FP64 solution: {err:.2e} (both to 1e-11, {its[0]} iterations)")
+    print(f"\n64^3 jump 1e4: batched vs FP64 solution {err:.2e} (both to 1e-10, {its[0]} iterations)")
     assert err <= 1e-8
+
+
+def test_solution_difference_at_jump_1e6():
+    """The 6.4 M-DoF workload with jump 1e6: FP64 and mixed solves to 5e-9
+    (the FP64 residual floor is 2.2e-9 here); the two solutions differ by
+    well under the 1e-8-residual solutions' own spread."""
+    N = 64
+    p = sphere_sinkers(N, 8, 0.08, 0.01, 1e6, device=DEV)
+    L = pkg.default_levels(N)
+    eta = torch.from_numpy(p.eta).to(DEV)
+    fbar = torch.from_numpy(p.fbar.ravel()).to(DEV)
+    xs = {}
+    for name, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
+        c = pkg.Context(N, L, prec, device=DEV)
+        c.prepare(eta, 10.0)
+        b = c.load_vector(fbar)
+        xs[name], its, rel = c.solve(b, 5e-9, 40000)
+        assert rel <= 5e-9
+        del c
+    err = _rel(xs["mixed"], xs["fp64"])
+    print(f"\n64^3 jump 1e6: mixed vs FP64 solution {err:.2e} (both to 5e-9)")
+    assert err <= 1e-6
 
 
 @pytest.fixture(scope="module")
