@@ -397,6 +397,22 @@ def agca_vs_dca(pkg, dev, stream):
     for name, nu, maxit in (("agca_nu10", NU, 20000), ("dca", NU_DCA, 20000)):
         res, _ = timed_solve(pkg, N, L, pkg.MIXED, eta, fbar, nu, dev, stream, maxit)
         out[name] = res
+    # the paper's outer solver on the same field: FGMRES + block-triangular + BFBT
+    c = pkg.Context(N, L, pkg.MIXED, device=dev, stream=stream)
+    c.prepare(eta, NU)
+    b = c.load_vector(fbar)
+    for zi in (10, 30):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        try:
+            _, its, rel = c.solve_fgmres(b, 1e-8, 600, 50, "bfbt", zi)
+        except pkg.AgcaError as e:
+            if e.status != 4:
+                raise
+            its, rel = 600, float("nan")
+        torch.cuda.synchronize(dev)
+        out[f"agca_nu10_fgmres_bfbt_zcg{zi}"] = {"iters": its, "relres": rel, "solve_s": time.perf_counter() - t0}
+    del c
     return out
 
 

@@ -20,10 +20,13 @@ class StokesProblem:
     """A fixed grid, forcing and solver configuration; theta varies."""
 
     def __init__(self, N: int, fbar: torch.Tensor, levels: int | None = None, precision: int = FP64,
-                 nu: float = 10.0, rtol: float = 1e-10, maxit: int = 20000, device="cuda"):
+                 nu: float = 10.0, rtol: float = 1e-10, maxit: int = 20000, device="cuda",
+                 rtol_adjoint: float | None = None):
         self.ctx = Context(N, levels, precision, device=device)
         self.fbar = fbar
         self.nu, self.rtol, self.maxit = nu, rtol, maxit
+        # the adjoint right-hand side (dJ/du) has its own attainable residual floor
+        self.rtol_adjoint = rtol if rtol_adjoint is None else rtol_adjoint
         self._theta_prepared = None  # copy of the theta the hierarchy was built for
         self.last_iters = (0, 0)
 
@@ -60,7 +63,7 @@ class _StokesVelocity(torch.autograd.Function):
         theta, x = fctx.saved_tensors
         problem = fctx.problem
         problem._prepare(theta)
-        g, its = problem.ctx.adjoint_gradient(x, grad_u.contiguous(), problem.rtol, problem.maxit)
+        g, its = problem.ctx.adjoint_gradient(x, grad_u.contiguous(), problem.rtol_adjoint, problem.maxit)
         problem.last_iters = (problem.last_iters[0], its)
         return g, None
 

@@ -223,10 +223,11 @@ template <typename T>
 cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, int ntasks, int64_t ntiles,
                                       cudaStream_t s);
 // whether a batched step of this kind runs the edge form: FP64 contexts keep
-// edge sums on every level, mixed ones on the finest level
+// edge sums on every level (the FP32 cycle keeps the per-cube kernel)
 template <typename TS, typename T>
 constexpr bool edge_form_step(int mode, bool coarse) {
-  return sizeof(TS) == sizeof(T) && mode != ST_STOKES && (sizeof(T) == 8 || !coarse);
+  (void)coarse;
+  return sizeof(TS) == 8 && sizeof(T) == 8 && mode != ST_STOKES;
 }
 
 // Element-wise batched tasks (transfers, conversions, coarsest solves).

@@ -36,7 +36,6 @@ struct Level {
   double* gca64 = nullptr;
   double* hedge = nullptr;  // FP64 contexts: per-vertex edge sums of the DCA coefficient [3][V] (edge form)
   double* coefm = nullptr;  // FP64 coarse levels: DCA coefficient with flagged elements zeroed (edge form)
-  float* hedge32 = nullptr; // mixed contexts, finest level: FP32 edge sums of eta [3][V] (edge form)
   // stencil storage of the flagged elements' Galerkin matrices (Remark 5)
   uint8_t* vmark = nullptr;   // vertex touched by a flagged element
   int32_t* sidx = nullptr;    // stencil index of a vertex or -1
@@ -199,7 +198,6 @@ void carve_workspace(agca_ctx* ctx, char* base) {
     }
     if (mixed) lv.mean32 = cv.take<float>(lv.E);
     if (!mixed) lv.hedge = cv.take<double>(3 * lv.V);
-    if (mixed && l == ctx->L) lv.hedge32 = cv.take<float>(3 * lv.V);
     if (!mixed && l < ctx->L) lv.coefm = cv.take<double>(lv.E);
     if (l < ctx->L) {
       lv.vmark = cv.take<uint8_t>(lv.V);
@@ -280,7 +278,6 @@ LevelOp<float> op32(const agca_ctx* ctx, int l) {
   op.h6 = (float)(1.0 / (6.0 * lv.n));
   op.hq = (float)(1.0 / (6.0 * (double)lv.n * lv.n));
   op.coef = lv.mean32;
-  if (l == ctx->L) op.hedge = lv.hedge32;
   if (l < ctx->L) {
     op.sidx = lv.sidx;
     op.sten = lv.n_sv > 0 ? lv.sten32 : nullptr;
@@ -723,7 +720,8 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
 // pressure block) or the diag(A)-BFBT of Eq. 4.2,
 //   S~^-1 = Z^-1 (B W^-1 A W^-1 B^T) Z^-1,  W = diag(A),  Z = B W^-1 B^T,
 // with Z applied matrix-free (one Stokes apply of [W^-1 B^T t; 0] gives both
-// Z t and A W^-1 B^T t) and Z^-1 by Jacobi-preconditioned conjugate
+// Z t and A W^-1 B^T t; in mixed contexts the preconditioner's Stokes applies
+// use FP32 arithmetic, the outer K z stays FP64) and Z^-1 by Jacobi-preconditioned conjugate
 // gradients on the mean-free pressures (diag(Z) probed with 27 colours: Z
 // couples pressure vertices at most 2 cells apart).  Arnoldi by classical
 // Gram-Schmidt with one reorthogonalisation (two block dot products and two
@@ -764,10 +762,10 @@ agca_status z_apply(agca_ctx* ctx, const FgmresWork& W, const double* p) {
   cudaStream_t s = ctx->stream;
   LK(1, launch_vec_op(VOP_ZERO, n3, W.t1, nullptr, nullptr, nullptr, nullptr, s));
   LK(1, launch_vec_op(VOP_COPY, np, W.t1 + n3, p, nullptr, nullptr, nullptr, s));
-  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // t2_u = B^T p
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, true));  // t2_u = B^T p
   LK(1, launch_vec_op(VOP_MUL, n3, W.t1, W.t2, ctx->lev[ctx->L].invD64, nullptr, nullptr, s));
   LK(1, launch_vec_op(VOP_ZERO, np, W.t1 + n3, nullptr, nullptr, nullptr, nullptr, s));
-  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // [A W^-1 B^T p; Z p]
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, true));  // [A W^-1 B^T p; Z p]
   return AGCA_OK;
 }
 
@@ -833,7 +831,7 @@ agca_status blocktri_precond(agca_ctx* ctx, const FgmresWork& W, const double* r
     CKS(z_apply(ctx, W, W.m));                              // t2_u = A W^-1 B^T t
     LK(1, launch_vec_op(VOP_MUL, n3, W.t1, W.t2, ctx->lev[ctx->L].invD64, nullptr, nullptr, s));
     LK(1, launch_vec_op(VOP_ZERO, np, W.t1 + n3, nullptr, nullptr, nullptr, nullptr, s));
-    CKS(stokes_dispatch(ctx, W.t1, W.t2, false));          // t2_p = B W^-1 A W^-1 B^T t
+    CKS(stokes_dispatch(ctx, W.t1, W.t2, true));          // t2_p = B W^-1 A W^-1 B^T t
     LK(1, launch_vec_op(VOP_COPY, np, W.m, W.t2 + n3, nullptr, nullptr, nullptr, s));
     CKS(z_solve(ctx, W, W.m, zp, z_iters));                 // S~^-1 r_p
   }
@@ -843,7 +841,7 @@ agca_status blocktri_precond(agca_ctx* ctx, const FgmresWork& W, const double* r
   // z_u = A~^-1 (r_u - B^T z_p)
   LK(1, launch_vec_op(VOP_ZERO, n3, W.t1, nullptr, nullptr, nullptr, nullptr, s));
   LK(1, launch_vec_op(VOP_COPY, np, W.t1 + n3, zp, nullptr, nullptr, nullptr, s));
-  CKS(stokes_dispatch(ctx, W.t1, W.t2, false));  // t2_u = B^T z_p
+  CKS(stokes_dispatch(ctx, W.t1, W.t2, true));  // t2_u = B^T z_p
   LK(1, launch_vec_op(VOP_SUB, n3, W.t1, r, W.t2, nullptr, nullptr, s));
   CKS(vcycle_impl(ctx, W.t1, z));
   return AGCA_OK;
@@ -1690,7 +1688,6 @@ agca_status agca_setup(agca_ctx* ctx) {
     }
     LK(1, launch_diag(op64(ctx, l), lv.diag, lv.invD64, mixed ? lv.invD32 : nullptr, s));
   }
-  if (mixed) LK(1, launch_edge_sums<float>(ctx->lev[L].n, ctx->lev[L].mean32, ctx->lev[L].hedge32, s));
   // coarsest operator: dense assembly, Cholesky, explicit inverse factor
   LK(1, launch_coarse_assemble(op64(ctx, 1), ctx->cdense, s));
   CK(cudaMemcpyAsync(ctx->cfac, ctx->cdense, (size_t)ctx->mc * ctx->mc * sizeof(double), cudaMemcpyDeviceToDevice, s));

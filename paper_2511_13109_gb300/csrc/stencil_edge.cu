@@ -60,6 +60,8 @@ __host__ __device__ constexpr size_t edge_smem_elems() {
          (size_t)3 * ENT;
 }
 // resident CTAs per SM the shared memory (and, in FP32, the register file) allows
+// (the FP32 form is not used: its per-copy staging arithmetic saturated the
+// integer pipe, 1600 instructions per vertex against 530 for the per-cube kernel)
 template <typename T, int MODE>
 __host__ __device__ constexpr int edge_min_blocks() {
   return sizeof(T) == 4 ? 3 : (MODE == ST_CHEB_PRE ? 1 : 2);
@@ -455,7 +457,6 @@ cudaError_t launch_edge_sums(int n, const T* eta, T* hedge, cudaStream_t s) {
   return launch_k(edge_sum_kernel<T>, dim3((unsigned)((V + 255) / 256)), dim3(256), 0, s, n, eta, hedge);
 }
 template cudaError_t launch_edge_sums<double>(int, const double*, double*, cudaStream_t);
-template cudaError_t launch_edge_sums<float>(int, const float*, float*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_stencil_edge(int mode, const LevelOp<T>& op, const StencilArgs<T>& a, cudaStream_t s, int zch_req) {
@@ -520,11 +521,7 @@ cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, 
 
 template cudaError_t launch_stencil_edge<double>(int, const LevelOp<double>&, const StencilArgs<double>&,
                                                   cudaStream_t, int);
-template cudaError_t launch_stencil_edge<float>(int, const LevelOp<float>&, const StencilArgs<float>&, cudaStream_t,
-                                                int);
 template cudaError_t launch_stencil_edge_batch<double>(int, const StencilTask<double, double>*, int, int64_t,
                                                        cudaStream_t);
-template cudaError_t launch_stencil_edge_batch<float>(int, const StencilTask<float, float>*, int, int64_t,
-                                                      cudaStream_t);
 
 }  // namespace agca

@@ -29,7 +29,7 @@ def small():
     c.prepare(torch.from_numpy(p.eta).to(DEV), 10.0)
     b = c.load_vector(torch.from_numpy(p.fbar.ravel()).to(DEV))
     bo = S.rhs(p.fbar)
-    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-15 * np.abs(bo).max()
+    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-14 * np.abs(bo).max()   # summation order
     return p, S, c, b, bo
 
 
