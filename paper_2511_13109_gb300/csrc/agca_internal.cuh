@@ -104,7 +104,7 @@ struct LevelOp {
   const int32_t* list; // flagged element ids (coarse levels)
   int64_t n_flag;      // number of flagged elements
   T* ye;               // n_flag * 12 scratch: s_e A_e x_e of the flagged elements
-  const T* hedge;      // FP64 levels: per-vertex edge sums of the DCA coefficient [3][V] (edge form), or nullptr
+  const T* hedge;      // FP64 levels: per-vertex coefficient records [EREC][V] of the edge form, or nullptr
   const T* coefm;      // FP64 coarse levels: DCA coefficient with flagged elements zeroed (edge form), or nullptr
   // stored-Galerkin part as per-vertex stencils (Remark 5): stencil index of a
   // vertex or -1, 15 x 3 x 3 couplings per touched vertex, FP32 scale (mixed)
@@ -193,12 +193,18 @@ struct TileGrid {
 };
 TileGrid stencil_tiles(int n, int by, int zch_req);
 
-// FP64 finest-level operator in edge form (stencil_edge.cu): modes APPLY,
-// RESID and the Chebyshev steps, with op.hedge = the per-vertex sums of eta
-// over the 6 tetrahedra around each forward axis edge (launch_edge_sums)
-TileGrid edge_tiles(int n, int zch_req);
+// Operator in edge form (stencil_edge.cu): modes APPLY, RESID and the
+// Chebyshev steps.  FP64: op.hedge = the per-vertex coefficient records
+// (EREC values per vertex, launch_edge_records): the sums of eta over the 6
+// tetrahedra around each forward axis edge and the weights of the edge
+// differences in the off-axis flux components.  FP32 (finest level): the
+// kernel forms the records from op.coef
+constexpr int EREC = 27;
+// tile grid of the edge form; zch_req 0 picks the z-chunk for `slots`
+// resident blocks (0: 304)
+TileGrid edge_tiles(int n, int zch_req, int slots = 0);
 template <typename T>
-cudaError_t launch_edge_sums(int n, const T* eta, T* hedge, cudaStream_t s);
+cudaError_t launch_edge_records(int n, const T* eta, T* rec, cudaStream_t s);
 template <typename T>
 cudaError_t launch_stencil_edge(int mode, const LevelOp<T>& op, const StencilArgs<T>& a, cudaStream_t s, int zch_req);
 
@@ -222,12 +228,13 @@ cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>
 template <typename T>
 cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, int ntasks, int64_t ntiles,
                                       cudaStream_t s);
-// whether a batched step of this kind runs the edge form: FP64 contexts keep
-// edge sums on every level (the FP32 cycle keeps the per-cube kernel)
+// whether a step of this kind runs the edge form: every level of an FP64
+// context (its coefficient records exist on every level) and the finest
+// level of the FP32 cycle (records formed in the kernel); the FP32 coarse
+// levels and the Stokes operator run the per-cube kernel
 template <typename TS, typename T>
 constexpr bool edge_form_step(int mode, bool coarse) {
-  (void)coarse;
-  return sizeof(TS) == 8 && sizeof(T) == 8 && mode != ST_STOKES;
+  return sizeof(TS) == sizeof(T) && mode != ST_STOKES && (sizeof(T) == 8 || !coarse);
 }
 
 // Element-wise batched tasks (transfers, conversions, coarsest solves).
@@ -329,7 +336,7 @@ cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t 
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s);
 // FGMRES pieces: out[i] = w . V_i (i < nvec, V_i = V + i ld); w += sign sum_i coef[i] V_i;
 // y = a * s or a / s (s on the device); conjugate-gradient updates on device scalars
-// sc[0] = rho, sc[1] = p.q, sc[2] = rho_new; pressure-grid colouring for probing a diagonal
+// sc[0] = rho, sc[1] = p.q, sc[2] = rho_new
 cudaError_t launch_block_dot(int nvec, const double* V, int64_t ld, const double* w, int64_t n, double* partials,
                              double* out, cudaStream_t s);
 cudaError_t launch_block_axpy(int nvec, const double* V, int64_t ld, const double* coef, double sign, double* w,
@@ -338,8 +345,12 @@ cudaError_t launch_scale(int64_t n, double* y, const double* a, const double* s_
 cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* sc,
                              cudaStream_t s);
 cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* sc, cudaStream_t s);
-cudaError_t launch_colour(int np, int colour, double* e, cudaStream_t s);
-cudaError_t launch_take_colour(int64_t n, const double* e, const double* y, double* d, cudaStream_t s);
+// assembled Z = B W^-1 B^T as per-vertex 5x5x5 stencils on the pressure grid
+// (zs: [V_p][125], offset (di, dj, dk) at (di+2) + 5 (dj+2) + 25 (dk+2))
+cudaError_t launch_colour5(int np, int colour, double* e, cudaStream_t s);
+cudaError_t launch_scatter_zrow(int np, int colour, const double* y, double* zs, cudaStream_t s);
+cudaError_t launch_zstencil(int np, const double* zs, const double* p, double* y, cudaStream_t s);
+cudaError_t launch_zdiag_inv(int np, const double* zs, double* dinv, cudaStream_t s);
 cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
                                cudaStream_t s);
 

@@ -34,7 +34,7 @@ struct Level {
   int32_t* list = nullptr;
   int64_t n_flag = 0;
   double* gca64 = nullptr;
-  double* hedge = nullptr;  // FP64 contexts: per-vertex edge sums of the DCA coefficient [3][V] (edge form)
+  double* hedge = nullptr;  // FP64 contexts: per-vertex coefficient records [EREC][V] of the edge form
   double* coefm = nullptr;  // FP64 coarse levels: DCA coefficient with flagged elements zeroed (edge form)
   // stencil storage of the flagged elements' Galerkin matrices (Remark 5)
   uint8_t* vmark = nullptr;   // vertex touched by a flagged element
@@ -197,7 +197,7 @@ void carve_workspace(agca_ctx* ctx, char* base) {
       lv.mn = lv.mean;
     }
     if (mixed) lv.mean32 = cv.take<float>(lv.E);
-    if (!mixed) lv.hedge = cv.take<double>(3 * lv.V);
+    if (!mixed) lv.hedge = cv.take<double>(EREC * lv.V);
     if (!mixed && l < ctx->L) lv.coefm = cv.take<double>(lv.E);
     if (l < ctx->L) {
       lv.vmark = cv.take<uint8_t>(lv.V);
@@ -344,16 +344,16 @@ double stencil_bytes(int mode, size_t s) {
 
 // Algorithmic arithmetic per vertex of one finest-level stencil launch (flops;
 // a fused multiply-add counts 2), from the edge form of Eq. 3.5 on a Kuhn
-// grid: per vertex 9 edge differences (3 axis edges x 3 components); per
-// tetrahedron 3 symmetrisations, 3 products eta * S off the diagonal, 3
-// products with 2 eta on it and the doubling of eta (6 x 10); the edge flux
-// sums over the 6 tetrahedra sharing each of the 3 axis edges (3 x 15); the
-// divergence of the 6 fluxes at the vertex (15): 129 in all.  The scaling by
-// h/6 folds into the epilogue (3 products, or a fused b - (h/6) y).  The
+// grid with the per-vertex coefficient records: 9 edge differences (3 axis
+// edges x 3 components); per axis edge the on-axis flux 2 H d (2) and two
+// off-axis components H d + four weighted differences (2 x 9); the
+// divergence of the 6 fluxes at the vertex (15): 84 in all (the
+// per-tetrahedron form of the same operator takes 129).  The scaling by h/6
+// folds into the epilogue (3 products, or a fused b - (h/6) y).  The
 // Chebyshev epilogues add per component: residual 2, first step 5, later
 // step 8, step from zero 7 plus 2 for its staged first iterate.
 double stencil_flops(int mode) {
-  const double op = 9.0 + 6.0 * 10.0 + 3.0 * 15.0 + 15.0;
+  const double op = 9.0 + 3.0 * (2.0 + 2.0 * 9.0) + 15.0;
   switch (mode) {
     case ST_APPLY: return op + 3.0;
     case ST_RESID: return op + 3.0 * 2.0;
@@ -719,16 +719,19 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
 // the mean-free lumped 1/eta pressure mass (the MINRES preconditioner's
 // pressure block) or the diag(A)-BFBT of Eq. 4.2,
 //   S~^-1 = Z^-1 (B W^-1 A W^-1 B^T) Z^-1,  W = diag(A),  Z = B W^-1 B^T,
-// with Z applied matrix-free (one Stokes apply of [W^-1 B^T t; 0] gives both
-// Z t and A W^-1 B^T t; in mixed contexts the preconditioner's Stokes applies
-// use FP32 arithmetic, the outer K z stays FP64) and Z^-1 by Jacobi-preconditioned conjugate
-// gradients on the mean-free pressures (diag(Z) probed with 27 colours: Z
-// couples pressure vertices at most 2 cells apart).  Arnoldi by classical
+// with the middle factor applied matrix-free (one Stokes apply of
+// [W^-1 B^T t; 0] gives A W^-1 B^T t) and Z assembled on the pressure grid as
+// it is in the paper (App. B): Z couples pressure vertices at most 2 cells
+// apart, so 125 applies of the matrix-free Z to colour indicators (vertices
+// equal mod 5 per axis) give every row as a 5x5x5 stencil; Z^-1 by
+// Jacobi-preconditioned conjugate gradients on the mean-free pressures.  In
+// mixed contexts the preconditioner's Stokes applies use FP32 arithmetic;
+// the outer K z stays FP64.  Arnoldi by classical
 // Gram-Schmidt with one reorthogonalisation (two block dot products and two
 // block updates per iteration); the small Hessenberg least-squares problem
 // by Givens rotations on the host.
 struct FgmresWork {
-  double *V, *Z, *w, *t1, *t2, *partials, *hbuf, *ycoef, *zdinv, *cx, *cr, *cz, *cp, *cq, *m, *sc;
+  double *V, *Z, *w, *t1, *t2, *partials, *hbuf, *ycoef, *zdinv, *cx, *cr, *cz, *cp, *cq, *m, *sc, *zsten;
   size_t need;
 };
 
@@ -752,6 +755,7 @@ FgmresWork fgmres_layout(const agca_ctx* ctx, int restart, char* base) {
   w.cq = cv.take<double>(np);
   w.m = cv.take<double>(np);
   w.sc = cv.take<double>(8);
+  w.zsten = cv.take<double>(np * 125);
   w.need = (cv.off + kAlign - 1) / kAlign * kAlign;
   return w;
 }
@@ -789,8 +793,7 @@ agca_status z_solve(agca_ctx* ctx, const FgmresWork& W, const double* rhs, doubl
   LK(1, launch_vec_op(VOP_COPY, np, W.cp, W.cz, nullptr, nullptr, nullptr, s));
   CKS(dot1(ctx, W.cr, W.cz, np, W.sc + 0));
   for (int it = 0; it < iters; ++it) {
-    CKS(z_apply(ctx, W, W.cp));
-    LK(1, launch_vec_op(VOP_COPY, np, W.cq, W.t2 + n3, nullptr, nullptr, nullptr, s));
+    LK(1, launch_zstencil(ctx->N, W.zsten, W.cp, W.cq, s));
     CKS(dot1(ctx, W.cp, W.cq, np, W.sc + 1));
     LK(1, launch_cg_update(np, x, W.cr, W.cp, W.cq, W.sc, s));
     LK(1, launch_vec_op(VOP_MUL, np, W.cz, W.cr, W.zdinv, nullptr, nullptr, s));
@@ -802,16 +805,16 @@ agca_status z_solve(agca_ctx* ctx, const FgmresWork& W, const double* rhs, doubl
   return AGCA_OK;
 }
 
-// diag(Z) by probing with the 27 colours (i mod 3, j mod 3, k mod 3), inverted
-agca_status z_diag(agca_ctx* ctx, const FgmresWork& W) {
-  const int64_t np = ctx->Vp, n3 = 3 * ctx->lev[ctx->L].V;
+// Z assembled by probing with the 125 colours (i, j, k) mod 5, and its inverse diagonal
+agca_status z_assemble(agca_ctx* ctx, const FgmresWork& W) {
+  const int64_t n3 = 3 * ctx->lev[ctx->L].V;
   cudaStream_t s = ctx->stream;
-  for (int c = 0; c < 27; ++c) {
-    LK(1, launch_colour(ctx->N, c, W.cp, s));
+  for (int c = 0; c < 125; ++c) {
+    LK(1, launch_colour5(ctx->N, c, W.cp, s));
     CKS(z_apply(ctx, W, W.cp));
-    LK(1, launch_take_colour(np, W.cp, W.t2 + n3, W.cq, s));
+    LK(1, launch_scatter_zrow(ctx->N, c, W.t2 + n3, W.zsten, s));
   }
-  LK(1, launch_vec_op(VOP_RECIP, np, W.zdinv, W.cq, nullptr, nullptr, nullptr, s));
+  LK(1, launch_zdiag_inv(ctx->N, W.zsten, W.zdinv, s));
   return AGCA_OK;
 }
 
@@ -857,7 +860,7 @@ agca_status fgmres_impl(agca_ctx* ctx, const FgmresWork& W, int restart, const d
   LK(1, launch_vec_op(VOP_COPY, nt, bm, b_in, nullptr, nullptr, nullptr, s));
   LK(1, launch_mask_boundary(ctx->lev[ctx->L].n, bm, s));
   LK(1, launch_vec_op(VOP_ZERO, nt, x, nullptr, nullptr, nullptr, nullptr, s));
-  if (schur == 1) CKS(z_diag(ctx, W));
+  if (schur == 1) CKS(z_assemble(ctx, W));
   double nb2 = 0.0;
   CKS(dot1(ctx, bm, bm, nt, ctx->sc + MS_TMP0));
   CKS(read_scalar(ctx, ctx->sc + MS_TMP0, &nb2));
@@ -978,7 +981,9 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   cudaStream_t s = ctx->stream;
   for (void* p : {lv.vb, lv.vx, lv.vt, lv.vr}) CK(cudaMemsetAsync(p, 0, n3 * sizeof(T), s));
   const bool f32 = sizeof(T) == 4;
-  std::vector<int> bys = f32 ? std::vector<int>{8, 12, 16} : std::vector<int>{8};
+  // the edge form (every FP64 level, the FP32 finest level) has one tile shape
+  const bool edge = !f32 || l == ctx->L;
+  std::vector<int> bys = edge ? std::vector<int>{8} : std::vector<int>{8, 12, 16};
   const int nv = lv.n + 1;
   int dev = 0, sms = 152;
   CK(cudaGetDevice(&dev));
@@ -988,8 +993,8 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   // partly filled last wave)
   auto candidates = [&](int by) {
     std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
-    const int per_sm = f32 ? (by <= 8 ? 3 : (by <= 12 ? 2 : 1)) : 2;
-    const int per_z = stencil_tiles(lv.n, by, 1).per_z();
+    const int per_sm = edge ? (f32 ? 3 : 2) : (by <= 8 ? 3 : (by <= 12 ? 2 : 1));
+    const int per_z = edge ? edge_tiles(lv.n, 1).per_z() : stencil_tiles(lv.n, by, 1).per_z();
     for (int k = 1; k <= 8; ++k) {
       const int gz = std::max(1, k * sms * per_sm / per_z);
       zs.push_back((nv + gz - 1) / gz);
@@ -1017,7 +1022,7 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
       int last_zch = -1;
       for (int zr : candidates(by)) {
         if (zr > nv) continue;
-        const int zch = stencil_tiles(lv.n, by, zr).zch;
+        const int zch = edge ? edge_tiles(lv.n, zr, (f32 ? 3 : 2) * sms).zch : stencil_tiles(lv.n, by, zr).zch;
         if (zch == last_zch) continue;
         last_zch = zch;
         TileCfg c;
@@ -1563,7 +1568,7 @@ agca_status agca_set_viscosity(agca_ctx* ctx, const double* eta_dev) {
   if (!ctx->ws) return ctx->fail(AGCA_ESTATE, "bind the workspace first");
   Level& lf = ctx->lev[ctx->L];
   CK(cudaMemcpyAsync(lf.mean, eta_dev, lf.E * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  if (lf.hedge) LK(1, launch_edge_sums(lf.n, lf.mean, lf.hedge, ctx->stream));
+  if (lf.hedge) LK(1, launch_edge_records(lf.n, lf.mean, lf.hedge, ctx->stream));
   ctx->have_eta = true;
   ctx->flagged = ctx->setup_done = false;
   return AGCA_OK;
@@ -1677,7 +1682,7 @@ agca_status agca_setup(agca_ctx* ctx) {
       LK(1, launch_stencil_to_f32(lc.n_sv, lc.sten64, lc.sten32, lc.sscale32, s));
     } else {
       LK(1, launch_masked_coef(lc.E, lc.mean, lc.fidx, lc.coefm, s));
-      LK(1, launch_edge_sums(lc.n, lc.coefm, lc.hedge, s));
+      LK(1, launch_edge_records(lc.n, lc.coefm, lc.hedge, s));
     }
   }
   for (int l = 1; l <= L; ++l) {

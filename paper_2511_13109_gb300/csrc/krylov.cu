@@ -342,22 +342,68 @@ __global__ void cg_shift_kernel(double* sc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = sc[2];  // rho <- rho_new
 }
 
-// indicator of the pressure vertices (i, j, k) with (i mod 3, j mod 3, k mod 3) = colour
-__global__ void colour_kernel(int np, int colour, double* __restrict__ e) {
+// Assembled Z = B W^-1 B^T on the pressure grid (np cubes per axis) as
+// per-vertex 5x5x5 stencils: Z couples pressure vertices at most 2 cells
+// apart, so applying Z to the indicator of colour (a, b, c) (vertices with
+// coordinates = (a, b, c) mod 5) yields, at every vertex l, the one entry
+// Z[l][k] of the colour vertex k within distance 2 of l.
+__global__ void colour5_kernel(int np, int colour, double* __restrict__ e) {
   grid_dep_entry();
   const int nv = np + 1;
   const int64_t V = (int64_t)nv * nv * nv;
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= V) return;
   const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
-  e[v] = (i % 3) + 3 * (j % 3) + 9 * (k % 3) == colour ? 1.0 : 0.0;
+  e[v] = (i % 5) + 5 * (j % 5) + 25 * (k % 5) == colour ? 1.0 : 0.0;
 }
-// d[v] = y[v] where e[v] = 1 (the colour's diagonal entries of the probed operator)
-__global__ void take_colour_kernel(int64_t n, const double* __restrict__ e, const double* __restrict__ y,
-                                   double* __restrict__ d) {
+__device__ __forceinline__ int offset5(int l, int c) {  // d in [-2, 2] with (l + d) mod 5 == c
+  return ((c - l % 5) + 7) % 5 - 2;
+}
+__global__ void scatter_zrow_kernel(int np, int colour, const double* __restrict__ y, double* __restrict__ zs) {
   grid_dep_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (e[i] != 0.0) d[i] = y[i];
+  const int nv = np + 1;
+  const int64_t V = (int64_t)nv * nv * nv;
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  const int di = offset5(i, colour % 5), dj = offset5(j, (colour / 5) % 5), dk = offset5(k, colour / 25);
+  zs[v * 125 + (di + 2) + 5 * (dj + 2) + 25 * (dk + 2)] = y[v];
+}
+// y = Z p from the assembled stencils (neighbours outside the grid contribute nothing)
+__global__ void zstencil_kernel(int np, const double* __restrict__ zs, const double* __restrict__ p,
+                                double* __restrict__ y) {
+  grid_dep_entry();
+  const int nv = np + 1;
+  const int64_t V = (int64_t)nv * nv * nv;
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  const double* row = zs + v * 125;
+  double acc = 0.0;
+  for (int dk = -2; dk <= 2; ++dk) {
+    const int kk = k + dk;
+    if (kk < 0 || kk > np) continue;
+    for (int dj = -2; dj <= 2; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj > np) continue;
+#pragma unroll
+      for (int di = -2; di <= 2; ++di) {
+        const int ii = i + di;
+        if (ii < 0 || ii > np) continue;
+        acc = fma(row[(di + 2) + 5 * (dj + 2) + 25 * (dk + 2)], __ldg(p + ii + (int64_t)nv * (jj + (int64_t)nv * kk)),
+                  acc);
+      }
+    }
+  }
+  y[v] = acc;
+}
+// inverse diagonal of the assembled Z (0 where it is not positive)
+__global__ void zdiag_inv_kernel(int64_t V, const double* __restrict__ zs, double* __restrict__ dinv) {
+  grid_dep_entry();
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double d = zs[v * 125 + 62];
+  dinv[v] = d > 0.0 ? 1.0 / d : 0.0;
 }
 
 }  // namespace
@@ -433,13 +479,23 @@ cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* s
   return cudaGetLastError();
 }
 
-cudaError_t launch_colour(int np, int colour, double* e, cudaStream_t s) {
-  KL(launch_k(colour_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, np, colour, e));
+cudaError_t launch_colour5(int np, int colour, double* e, cudaStream_t s) {
+  KL(launch_k(colour5_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, np, colour, e));
   return cudaGetLastError();
 }
 
-cudaError_t launch_take_colour(int64_t n, const double* e, const double* y, double* d, cudaStream_t s) {
-  KL(launch_k(take_colour_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, e, y, d));
+cudaError_t launch_scatter_zrow(int np, int colour, const double* y, double* zs, cudaStream_t s) {
+  KL(launch_k(scatter_zrow_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, np, colour, y, zs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zstencil(int np, const double* zs, const double* p, double* y, cudaStream_t s) {
+  KL(launch_k(zstencil_kernel, dim3(blocks_for(nverts(np), 128)), dim3(128), 0, s, np, zs, p, y));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zdiag_inv(int np, const double* zs, double* dinv, cudaStream_t s) {
+  KL(launch_k(zdiag_inv_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, nverts(np), zs, dinv));
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
-// FP64 finest-level operator in edge form (Eq. 2.3 with the element matrices
-// of Eq. 3.5), fused with the smoother and residual epilogues.
+// Finest-level operator in edge form (Eq. 2.3 with the element matrices of
+// Eq. 3.5), fused with the smoother and residual epilogues: every level of
+// an FP64 context and the finest level of the FP32 cycle.
 //
 // On a Kuhn grid every edge of a tetrahedron's path is an axis edge of the
 // grid, and the element action reduces to fluxes along those edges (see
@@ -11,24 +12,34 @@
 //   F_E[c] = H_E d_E[c] + sum_{t around E} eta_t d_{e_t(c)}[m]   (c != m),
 // where H_E is the sum of eta_t around E and e_t(c) the c-edge of t's path,
 // and the operator is y_v = (h/6) sum_m (F_(v - e_m, m) - F_(v, m)).
-// Per vertex this is 9 edge differences, 3 x 16 flux products and 15
-// divergence terms: about 75 FP64 instructions against about 190 for the
-// per-tetrahedron form.  FP64 arithmetic is the bound of this operator on
-// GB300 (one FP64 fused multiply-add per 64 FP32 ones), so the per-vertex
-// edge sums H (3 per vertex) are formed once per set-up (edge_sum_kernel)
-// and the neighbours' edge differences are shared through shared memory
-// instead of being recomputed.
+// Per vertex the coefficients enter through a record of 27 combinations
+// (EREC, edge_record): the three edge sums H_m and, for each forward edge m
+// and component c != m, the weights of the four distinct c-edge differences
+// around the edge (two of them the sum of the two tetrahedra sharing that
+// difference).  The kernel then does 9 edge differences, 3 x 20 flux flops
+// and 15 divergence terms per vertex, against about 190 for the
+// per-tetrahedron form; the neighbours' edge differences are shared through
+// shared memory instead of being recomputed.
+//
+// FP64: GB300 runs one FP64 fused multiply-add per 64 FP32 ones, so FP64
+// arithmetic bounds the operator; the records are formed once per viscosity
+// (edge_record_kernel) and read by each vertex's own thread.  FP32: memory
+// bounds it; the records are formed in the kernel from cube-coefficient rows
+// staged in shared memory (6 values per cube instead of 27 per vertex).
 //
 // Tiling: a CTA of 32 x 8 threads, thread (tx, ty) <-> vertex column
 // (x0 - 1 + tx, y0 - 1 + ty), marches a chunk of z-planes.  Per plane k it
-// stages the x plane k + 2 (cp.async, one plane ahead), forms the edge
-// differences of plane k + 1 for its (34 x 10)-vertex tile, computes the three
-// fluxes of its vertex's forward edges from the differences of planes
-// k - 1..k + 1 and the coefficients of cube layers k - 1, k, exchanges the x
-// and y fluxes through shared memory (the z flux stays in registers for the
-// next plane), and the threads with tx, ty >= 1 finish their vertex
-// (owner-computes: no atomics; every vertex sums its fluxes in one fixed
-// order, whatever the tile shape or z-chunk).
+// stages the x plane k + 2 (cp.async, one plane ahead; FP32: the cube layer
+// k + 1 too), forms the edge differences of plane k + 1 for its
+// (34 x 10)-vertex tile, computes the three fluxes of its vertex's forward
+// edges from the differences of planes k - 1..k + 1 and its vertex's
+// coefficient record, exchanges the x and y fluxes (warp shuffle, shared
+// memory; the z flux stays in registers for the next plane), and the threads
+// with tx, ty >= 1 finish their vertex (owner-computes: no atomics; every
+// vertex sums its fluxes in one fixed order, whatever the tile shape or
+// z-chunk).  Staging copies whole tile rows per warp: a row's geometry is
+// warp-uniform and each lane's column bounds are fixed for the block, so a
+// copy costs an address add and a predicate.
 #include <algorithm>
 
 #include "agca_internal.cuh"
@@ -38,11 +49,14 @@ namespace agca {
 
 namespace {
 
-constexpr int EBX = 32, EBY = 8, ENT = EBX * EBY;
+constexpr int EBX = 32, EBY = 8, ENT = EBX * EBY, NWARP = ENT / 32;
 constexpr int XW = EBX + 3, XH = EBY + 3, XT = XW * XH;  // x tile: vertices (x0-2 .., y0-2 ..)
 constexpr int DW = EBX + 2, DH = EBY + 2, DT = DW * DH;  // edge-difference tile
-constexpr int CW = EBX + 1, CH = EBY + 1, CT = CW * CH;  // cube tile: origins (x0-2 .., y0-2 ..)
-constexpr int DRING = 84;                                // halo entries of the difference tile
+constexpr int CW = EBX + 1, CH = EBY + 1, CROW = 6 * CW;  // FP32 cube tile: origins (x0-2 .., y0-2 ..)
+constexpr int CIT = (CROW + 31) / 32;                      // warp copies per cube-tile row
+constexpr int DRING = 84;                                  // halo entries of the difference tile
+static_assert(EBX == 32, "a tile row is one warp");
+static_assert(XW - 32 <= 32 && CIT <= 8, "row staging covers a row in at most 2 (x) / 8 (cubes) warp copies");
 // off-diagonal edge-difference components kept in shared memory:
 // (edge axis, component) = xy, xz, yx, yz, zx, zy
 enum { XY = 0, XZ, YX, YZ, ZX, ZY };
@@ -50,21 +64,25 @@ enum { XY = 0, XZ, YX, YZ, ZX, ZY };
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int MODE>
+// the records come from HBM in FP64 and from staged cube rows in FP32
+template <typename T>
+__host__ __device__ constexpr bool edge_stored_records() {
+  return sizeof(T) == 8;
+}
+template <typename T, int MODE>
 __host__ __device__ constexpr size_t edge_smem_elems() {
   // x ring [3][3][XT] (+ D^-1 ring for the step from zero), difference ring
-  // [3][6][DT], coefficient ring [2][6][CT], y-flux exchange [3][ENT]: in
-  // FP64 111 KB (two CTAs per SM) or, with the D^-1 ring, 139 KB; in FP32
-  // half of that (three CTAs per SM)
-  return (size_t)(MODE == ST_CHEB_PRE ? 2 : 1) * 3 * 3 * XT + (size_t)3 * 6 * DT + (size_t)2 * 6 * CT +
-         (size_t)3 * ENT;
+  // [3][6][DT], FP32 cube ring [2][CH][CROW], y-flux exchange [3][ENT]:
+  // FP64 82 KB (110 KB with the D^-1 ring), two CTAs per SM; FP32 56 KB
+  // (70 KB), three CTAs per SM
+  return (size_t)(MODE == ST_CHEB_PRE ? 2 : 1) * 3 * 3 * XT + (size_t)3 * 6 * DT +
+         (edge_stored_records<T>() ? 0 : (size_t)2 * CH * CROW) + (size_t)3 * ENT;
 }
-// resident CTAs per SM the shared memory (and, in FP32, the register file) allows
-// (the FP32 form is not used: its per-copy staging arithmetic saturated the
-// integer pipe, 1600 instructions per vertex against 530 for the per-cube kernel)
+// resident CTAs per SM (shared memory and the register budget: 128 per
+// thread in FP64, 85 in FP32)
 template <typename T, int MODE>
 __host__ __device__ constexpr int edge_min_blocks() {
-  return sizeof(T) == 4 ? 3 : (MODE == ST_CHEB_PRE ? 1 : 2);
+  return sizeof(T) == 8 ? 2 : 3;
 }
 template <typename T>
 __device__ __forceinline__ void cpT(T* smem, const T* gmem, bool ok) {
@@ -74,6 +92,31 @@ __device__ __forceinline__ void cpT(T* smem, const T* gmem, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(src) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src) : "memory");
+}
+
+// The coefficient record of vertex v = (i, j, k) from the coefficients of
+// the cubes around it, named by the cube's offset from v and the tetrahedron
+// type: v0..v5 cube (i, j, k); mx cube (i-1, j, k), my (i, j-1, k),
+// mxy (i-1, j-1, k), mz (i, j, k-1), myz (i, j-1, k-1), mxz (i-1, j, k-1)
+// (0 for a cube outside the grid).
+//   q = 0..2   H_x, H_y, H_z (sums over the 6 tetrahedra around each edge)
+//   q = 3..10  x edge: component y, then z
+//   q = 11..18 y edge: component x, then z
+//   q = 19..26 z edge: component x, then y
+// each (edge, component) block holding the weights of its four difference
+// terms in the order stencil_edge_block reads them; the four add up to H_m.
+template <typename T>
+__device__ __forceinline__ void edge_record(T v0, T v1, T v2, T v3, T v4, T v5, T mx0, T mx1, T my2, T my3, T mxy0,
+                                            T mxy2, T mz4, T mz5, T myz3, T myz5, T mxz1, T mxz4, T (&r)[EREC]) {
+  r[0] = ((v0 + v1) + (my2 + mz4)) + (myz3 + myz5);
+  r[1] = ((v2 + v3) + (mx0 + mz5)) + (mxz1 + mxz4);
+  r[2] = ((v4 + v5) + (mx1 + my3)) + (mxy0 + mxy2);
+  r[3] = v0 + mz4, r[4] = my2 + myz5, r[5] = v1, r[6] = myz3;
+  r[7] = v1 + my2, r[8] = mz4 + myz3, r[9] = v0, r[10] = myz5;
+  r[11] = v2 + mz5, r[12] = mx0 + mxz4, r[13] = v3, r[14] = mxz1;
+  r[15] = v3 + mx0, r[16] = mz5 + mxz1, r[17] = v2, r[18] = mxz4;
+  r[19] = v4 + my3, r[20] = mx1 + mxy2, r[21] = v5, r[22] = mxy0;
+  r[23] = v5 + mx1, r[24] = my3 + mxy0, r[25] = v4, r[26] = mxy2;
 }
 
 // difference-tile coordinates of halo entry r (0..83): rows 0 and DH-1, then
@@ -94,40 +137,64 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
                                                    const int x0, const int y0, const int bz, const int tid,
                                                    T* __restrict__ sm) {
   const int n = op.n, nv = n + 1, V = nv * nv * nv;
-  const int tx = tid & (EBX - 1), ty = tid >> 5;
+  const int tx = tid & (EBX - 1), ty = tid >> 5;  // lane, warp
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const int za = bz * zch, zb = min(za + zch, nv);
   const bool owner = tx >= 1 && ty >= 1 && gx <= n && gy <= n;
   const bool inner_xy = gx > 0 && gx < n && gy > 0 && gy < n;
   constexpr bool PRE = MODE == ST_CHEB_PRE;
+  constexpr bool STORED = edge_stored_records<T>();
 
   T* xs = sm;                                    // [3][3][XT]
   T* xa = xs + 3 * 3 * XT;                       // PRE: D^-1 ring [3][3][XT]
   T* ds = xa + (PRE ? 3 * 3 * XT : 0);           // [3][6][DT]
-  T* cs = ds + 3 * 6 * DT;                       // [2][6][CT]
-  T* fy = cs + 2 * 6 * CT;                       // [3][ENT]
+  T* cs = ds + 3 * 6 * DT;                       // FP32: cube ring [2][CH][CROW]
+  T* fy = cs + (STORED ? 0 : 2 * CH * CROW);     // [3][ENT]
+  const T* coefp = op.coefm ? op.coefm : op.coef;
 
   const int zs = za - 2;  // planes zs + i use ring slot i mod 3, cube layers zs + i slot i mod 2
   auto slot = [&](int p) { return (p - zs) % 3; };
   auto cslot = [&](int q) { return (q - zs) & 1; };
 
-  // stage x plane p (PRE: b and D^-1) for the x tile; Dirichlet and outside
-  // vertices read as zero
+  // this lane's columns of the x tile (x0 - 2 + tx, and x0 + 30 + tx for the
+  // last XW - 32 lanes): interior in x?  Dirichlet and outside vertices read 0
+  const bool inx0 = x0 - 2 + tx > 0 && x0 - 2 + tx < n;
+  const bool inx1 = tx < XW - 32 && x0 + 30 + tx > 0 && x0 + 30 + tx < n;
+  // FP32: bit it set if element it * 32 + tx of a cube-tile row lies on a cube
+  // inside the grid in x
+  unsigned cmask = 0;
+  if (!STORED) {
+#pragma unroll
+    for (int it = 0; it < CIT; ++it) {
+      const int e = it * 32 + tx, cx = x0 - 2 + e / 6;
+      if (e < CROW && cx >= 0 && cx < n) cmask |= 1u << it;
+    }
+  }
+
+  // stage x plane p (PRE: b and D^-1): warp ty copies the rows r = ty, ty + 8, ..
+  // of the [3][XH] rows of the tile
   auto issue_x = [&](int p) {
     T* dst = xs + slot(p) * 3 * XT;
     T* dsa = xa + slot(p) * 3 * XT;
     const bool zin = p > 0 && p < n;
-    for (int e = tid; e < 3 * XT; e += ENT) {
-      const int c = e / XT, r = e - c * XT;
-      const int j = r / XW, i = r - j * XW;
-      const int vx = x0 - 2 + i, vy = y0 - 2 + j;
-      const bool in = zin && vx > 0 && vx < n && vy > 0 && vy < n;
-      const int g = in ? c * V + vx + nv * (vy + nv * p) : 0;
+    for (int r = ty; r < 3 * XH; r += NWARP) {
+      const int c = r / XH, j = r - c * XH;
+      const int vy = y0 - 2 + j;
+      const bool rin = zin && vy > 0 && vy < n;
+      const int g = c * V + (x0 - 2) + nv * (vy + nv * p);  // valid when rin (then vy >= 1, so g >= 0)
+      const int e = c * XT + j * XW + tx;
+      const bool ok0 = rin && inx0, ok1 = rin && inx1;
+      const int g0 = ok0 ? g + tx : 0, g1 = ok1 ? g + 32 + tx : 0;
       if (PRE) {
-        cpT(dst + e, a.b + g, in);
-        cpT(dsa + e, a.invD + g, in);
+        cpT(dst + e, a.b + g0, ok0);
+        cpT(dsa + e, a.invD + g0, ok0);
+        if (tx < XW - 32) {
+          cpT(dst + e + 32, a.b + g1, ok1);
+          cpT(dsa + e + 32, a.invD + g1, ok1);
+        }
       } else {
-        cpT(dst + e, a.x + g, in);
+        cpT(dst + e, a.x + g0, ok0);
+        if (tx < XW - 32) cpT(dst + e + 32, a.x + g1, ok1);
       }
     }
   };
@@ -137,19 +204,26 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     if (!PRE) return;
     T* dst = xs + slot(p) * 3 * XT;
     const T* dsa = xa + slot(p) * 3 * XT;
-    for (int e = tid; e < 3 * XT; e += ENT) dst[e] = a.s2 * dsa[e] * dst[e];
+    for (int r = ty; r < 3 * XH; r += NWARP) {
+      const int c = r / XH, j = r - c * XH;
+      const int e = c * XT + j * XW + tx;
+      dst[e] = a.s2 * dsa[e] * dst[e];
+      if (tx < XW - 32) dst[e + 32] = a.s2 * dsa[e + 32] * dst[e + 32];
+    }
   };
-  // stage the 6 coefficients of every cube of the cube tile on layer q
+  // FP32: stage the cube layer q of the cube tile, rows of 6 CW contiguous
+  // coefficients in the global layout; warp ty copies the (row, part) pairs
+  // u = ty, ty + 8, .. of the CH x CIT pairs
   auto issue_coef = [&](int q) {
-    T* dst = cs + cslot(q) * 6 * CT;
+    if (STORED) return;
+    T* dst = cs + cslot(q) * CH * CROW;
     const bool qin = q >= 0 && q < n;
-    for (int e = tid; e < 6 * CT; e += ENT) {
-      const int j = e / (6 * CW), r = e - j * 6 * CW;
-      const int i = r / 6, t = r - i * 6;
-      const int cx = x0 - 2 + i, cy = y0 - 2 + j;
-      const bool in = qin && cx >= 0 && cx < n && cy >= 0 && cy < n;
-      const int g = in ? 6 * (cx + n * (cy + n * q)) + t : 0;
-      cpT(dst + t * CT + j * CW + i, (op.coefm ? op.coefm : op.coef) + g, in);
+    for (int u = ty; u < CH * CIT; u += NWARP) {
+      const int j = u / CIT, it = u - j * CIT;
+      const int cy = y0 - 2 + j, e = it * 32 + tx;
+      const bool ok = qin && cy >= 0 && cy < n && ((cmask >> it) & 1u);
+      const int g = ok ? 6 * ((x0 - 2) + n * (cy + n * q)) + e : 0;
+      if (e < CROW) cpT(dst + j * CROW + e, coefp + g, ok);
     }
   };
   // edge differences of plane p from x planes p, p + 1: difference-tile
@@ -189,7 +263,7 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     }
   };
 
-  // prologue: x planes za-2 .. za, coefficient layers za-2, za-1; edge
+  // prologue: x planes za-2 .. za (FP32: cube layers za-2, za-1); edge
   // differences of planes za-2 and za-1
   issue_x(zs);
   issue_x(zs + 1);
@@ -215,19 +289,29 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
   for (int k = za - 1; k < zb; ++k) {
     cp_wait_all();
     convert_x(k + 2);
-    __syncthreads();  // x plane k+2 and coefficient layer k staged; ring slots of k-2 free
+    __syncthreads();  // x plane k+2 (FP32: cube layer k) staged; ring slots of k-2 free
     compute_d(k + 1, dnext);
     __syncthreads();  // differences of plane k+1 visible; x slot of plane k free
     if (k + 1 < zb) issue_x(k + 3);
     cp_commit();
 
-    // own edge sums and epilogue inputs of plane k, read early
+    // own coefficient record and epilogue inputs of plane k, read early
     const bool kin = k >= 0 && k <= n && gx >= 0 && gx <= n && gy >= 0 && gy <= n;
     const int vo = kin ? gx + nv * (gy + nv * k) : 0;
-    T H[3] = {T(0), T(0), T(0)};
-    if (kin) {
+    T R[EREC];
+    if (STORED) {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) H[m] = __ldg(op.hedge + m * V + vo);
+      for (int q = 0; q < EREC; ++q) R[q] = kin ? __ldg(op.hedge + (int64_t)q * V + vo) : T(0);
+    } else {
+      // the 7 cubes around the vertex that touch its forward edges, from cube
+      // layers k - 1 and k (zero outside the grid)
+      const T* cm = cs + cslot(k - 1) * CH * CROW;
+      const T* c0 = cs + cslot(k) * CH * CROW;
+      auto C = [&](const T* p, int t, int di, int dj) { return p[(J + dj) * CROW + (I + di) * 6 + t]; };
+      edge_record<T>(C(c0, 0, 0, 0), C(c0, 1, 0, 0), C(c0, 2, 0, 0), C(c0, 3, 0, 0), C(c0, 4, 0, 0), C(c0, 5, 0, 0),
+                     C(c0, 0, -1, 0), C(c0, 1, -1, 0), C(c0, 2, 0, -1), C(c0, 3, 0, -1), C(c0, 0, -1, -1),
+                     C(c0, 2, -1, -1), C(cm, 4, 0, 0), C(cm, 5, 0, 0), C(cm, 3, 0, -1), C(cm, 5, 0, -1),
+                     C(cm, 1, -1, 0), C(cm, 4, -1, 0), R);
     }
     const bool out_k = owner && k >= za;
     const bool inner = out_k && inner_xy && k > 0 && k < n;
@@ -245,78 +329,29 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     const T* dm = ds + slot(k - 1) * 6 * DT;  // plane k-1
     const T* d0 = ds + slot(k) * 6 * DT;      // plane k
     const T* dp = ds + slot(k + 1) * 6 * DT;  // plane k+1
-    const T* cm = cs + cslot(k - 1) * 6 * CT;  // cube layer k-1
-    const T* c0 = cs + cslot(k) * 6 * CT;      // cube layer k
     auto D = [&](const T* p, int comp, int di, int dj) { return p[comp * DT + (J + dj) * DW + I + di]; };
-    auto C = [&](const T* p, int t, int di, int dj) { return p[t * CT + (J + dj) * CW + I + di]; };
-    // coefficients of the 7 cubes around the vertex that touch its forward edges
-    const T v0 = C(c0, 0, 0, 0), v1 = C(c0, 1, 0, 0), v2 = C(c0, 2, 0, 0), v3 = C(c0, 3, 0, 0),
-                 v4 = C(c0, 4, 0, 0), v5 = C(c0, 5, 0, 0);
-    const T mx0 = C(c0, 0, -1, 0), mx1 = C(c0, 1, -1, 0);      // cube v - ex
-    const T my2 = C(c0, 2, 0, -1), my3 = C(c0, 3, 0, -1);      // v - ey
-    const T mxy0 = C(c0, 0, -1, -1), mxy2 = C(c0, 2, -1, -1);  // v - ex - ey
-    const T mz4 = C(cm, 4, 0, 0), mz5 = C(cm, 5, 0, 0);        // v - ez
-    const T myz3 = C(cm, 3, 0, -1), myz5 = C(cm, 5, 0, -1);    // v - ey - ez
-    const T mxz1 = C(cm, 1, -1, 0), mxz4 = C(cm, 4, -1, 0);    // v - ex - ez
 
     T Fx[3], Fy[3], Fz[3];
+    // flux component c != m of edge m: the H_m term and the four distinct
+    // c-edge differences around the edge, weighted by the record (EREC order)
+    auto flux = [&](int q0, T hd, T da, T db, T dc, T dd) {
+      T f = fma(da, R[q0], hd);
+      f = fma(db, R[q0 + 1], f);
+      f = fma(dc, R[q0 + 2], f);
+      return fma(dd, R[q0 + 3], f);
+    };
     // x edge (v, v + ex)
-    {
-      const T h = H[0];
-      Fx[0] = T(2) * (h * dcur[0][0]);
-      T s = h * dcur[0][1];
-      s = fma(D(d0, YX, 1, 0), v0, s);
-      s = fma(D(d0, YX, 1, 0), mz4, s);
-      s = fma(D(d0, YX, 0, -1), my2, s);
-      s = fma(D(d0, YX, 0, -1), myz5, s);
-      s = fma(D(dp, YX, 1, 0), v1, s);
-      Fx[1] = fma(D(dm, YX, 0, -1), myz3, s);
-      s = h * dcur[0][2];
-      s = fma(D(d0, ZX, 1, 0), v1, s);
-      s = fma(D(d0, ZX, 1, 0), my2, s);
-      s = fma(D(dm, ZX, 0, 0), mz4, s);
-      s = fma(D(dm, ZX, 0, 0), myz3, s);
-      s = fma(D(d0, ZX, 1, 1), v0, s);
-      Fx[2] = fma(D(dm, ZX, 0, -1), myz5, s);
-    }
+    Fx[0] = T(2) * (R[0] * dcur[0][0]);
+    Fx[1] = flux(3, R[0] * dcur[0][1], D(d0, YX, 1, 0), D(d0, YX, 0, -1), D(dp, YX, 1, 0), D(dm, YX, 0, -1));
+    Fx[2] = flux(7, R[0] * dcur[0][2], D(d0, ZX, 1, 0), D(dm, ZX, 0, 0), D(d0, ZX, 1, 1), D(dm, ZX, 0, -1));
     // y edge (v, v + ey)
-    {
-      const T h = H[1];
-      Fy[1] = T(2) * (h * dcur[1][1]);
-      T s = h * dcur[1][0];
-      s = fma(D(d0, XY, 0, 1), v2, s);
-      s = fma(D(d0, XY, 0, 1), mz5, s);
-      s = fma(D(d0, XY, -1, 0), mx0, s);
-      s = fma(D(d0, XY, -1, 0), mxz4, s);
-      s = fma(D(dp, XY, 0, 1), v3, s);
-      Fy[0] = fma(D(dm, XY, -1, 0), mxz1, s);
-      s = h * dcur[1][2];
-      s = fma(D(d0, ZY, 0, 1), v3, s);
-      s = fma(D(d0, ZY, 0, 1), mx0, s);
-      s = fma(D(dm, ZY, 0, 0), mz5, s);
-      s = fma(D(dm, ZY, 0, 0), mxz1, s);
-      s = fma(D(d0, ZY, 1, 1), v2, s);
-      Fy[2] = fma(D(dm, ZY, -1, 0), mxz4, s);
-    }
+    Fy[1] = T(2) * (R[1] * dcur[1][1]);
+    Fy[0] = flux(11, R[1] * dcur[1][0], D(d0, XY, 0, 1), D(d0, XY, -1, 0), D(dp, XY, 0, 1), D(dm, XY, -1, 0));
+    Fy[2] = flux(15, R[1] * dcur[1][2], D(d0, ZY, 0, 1), D(dm, ZY, 0, 0), D(d0, ZY, 1, 1), D(dm, ZY, -1, 0));
     // z edge (v, v + ez)
-    {
-      const T h = H[2];
-      Fz[2] = T(2) * (h * dcur[2][2]);
-      T s = h * dcur[2][0];
-      s = fma(D(dp, XZ, 0, 0), v4, s);
-      s = fma(D(dp, XZ, 0, 0), my3, s);
-      s = fma(D(d0, XZ, -1, 0), mx1, s);
-      s = fma(D(d0, XZ, -1, 0), mxy2, s);
-      s = fma(D(dp, XZ, 0, 1), v5, s);
-      Fz[0] = fma(D(d0, XZ, -1, -1), mxy0, s);
-      s = h * dcur[2][1];
-      s = fma(D(dp, YZ, 0, 0), v5, s);
-      s = fma(D(dp, YZ, 0, 0), mx1, s);
-      s = fma(D(d0, YZ, 0, -1), my3, s);
-      s = fma(D(d0, YZ, 0, -1), mxy0, s);
-      s = fma(D(dp, YZ, 1, 0), v4, s);
-      Fz[1] = fma(D(d0, YZ, -1, -1), mxy2, s);
-    }
+    Fz[2] = T(2) * (R[2] * dcur[2][2]);
+    Fz[0] = flux(19, R[2] * dcur[2][0], D(dp, XZ, 0, 0), D(d0, XZ, -1, 0), D(dp, XZ, 0, 1), D(d0, XZ, -1, -1));
+    Fz[1] = flux(23, R[2] * dcur[2][1], D(dp, YZ, 0, 0), D(d0, YZ, 0, -1), D(dp, YZ, 1, 0), D(d0, YZ, -1, -1));
     // the x edge ending at v belongs to lane tx - 1 of the same row (a warp)
     T fl[3];
 #pragma unroll
@@ -324,9 +359,11 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
       fl[c] = __shfl_up_sync(0xffffffffu, Fx[c], 1);
       fy[c * ENT + tid] = Fy[c];
     }
-    __syncthreads();  // y fluxes of the tile visible; coefficient layer k-1 free
-    if (k + 1 < zb) issue_coef(k + 1);
-    cp_commit();
+    __syncthreads();  // y fluxes of the tile visible; FP32: cube layer k-1 free
+    if (!STORED) {
+      if (k + 1 < zb) issue_coef(k + 1);
+      cp_commit();
+    }
     T gs[3] = {T(0), T(0), T(0)};  // stored-Galerkin part (coarse levels)
     if (op.sten && inner) {
       const int sv = op.sidx[vo];
@@ -408,11 +445,9 @@ __global__ void __launch_bounds__(ENT, edge_min_blocks<T, MODE>())
   }
 }
 
-// H[m][v] = sum of eta over the 6 tetrahedra around the edge (v, v + e_m)
-// (0 where the edge leaves the grid), in a fixed order; cube offsets and
-// types as in stencil_edge_block
+// the coefficient record of every vertex, rec[q][v], q < EREC (edge_record)
 template <typename T>
-__global__ void edge_sum_kernel(const int n, const T* __restrict__ eta, T* __restrict__ hedge) {
+__global__ void edge_record_kernel(const int n, const T* __restrict__ eta, T* __restrict__ rec) {
   const int nv = n + 1;
   const int64_t V = (int64_t)nv * nv * nv;
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -423,16 +458,18 @@ __global__ void edge_sum_kernel(const int n, const T* __restrict__ eta, T* __res
     if (ci < 0 || cj < 0 || ck < 0 || ci >= n || cj >= n || ck >= n) return T(0);
     return __ldg(eta + 6 * (ci + (int64_t)n * (cj + (int64_t)n * ck)) + t);
   };
-  hedge[v] = ((c(0, 0, 0, 0) + c(0, 0, 0, 1)) + (c(0, -1, 0, 2) + c(0, 0, -1, 4))) + (c(0, -1, -1, 3) + c(0, -1, -1, 5));
-  hedge[V + v] =
-      ((c(0, 0, 0, 2) + c(0, 0, 0, 3)) + (c(-1, 0, 0, 0) + c(0, 0, -1, 5))) + (c(-1, 0, -1, 1) + c(-1, 0, -1, 4));
-  hedge[2 * V + v] =
-      ((c(0, 0, 0, 4) + c(0, 0, 0, 5)) + (c(-1, 0, 0, 1) + c(0, -1, 0, 3))) + (c(-1, -1, 0, 0) + c(-1, -1, 0, 2));
+  T r[EREC];
+  edge_record<T>(c(0, 0, 0, 0), c(0, 0, 0, 1), c(0, 0, 0, 2), c(0, 0, 0, 3), c(0, 0, 0, 4), c(0, 0, 0, 5),
+                 c(-1, 0, 0, 0), c(-1, 0, 0, 1), c(0, -1, 0, 2), c(0, -1, 0, 3), c(-1, -1, 0, 0), c(-1, -1, 0, 2),
+                 c(0, 0, -1, 4), c(0, 0, -1, 5), c(0, -1, -1, 3), c(0, -1, -1, 5), c(-1, 0, -1, 1), c(-1, 0, -1, 4),
+                 r);
+#pragma unroll
+  for (int q = 0; q < EREC; ++q) rec[q * V + v] = r[q];
 }
 
 }  // namespace
 
-TileGrid edge_tiles(int n, int zch_req) {
+TileGrid edge_tiles(int n, int zch_req, int slots) {
   const int nv = n + 1;
   TileGrid g;
   g.gxw = (nv + EBX - 2) / (EBX - 1);
@@ -440,10 +477,24 @@ TileGrid edge_tiles(int n, int zch_req) {
   g.gxn = g.gyn = 0;
   g.x0n = 31 * g.gxw;
   const int per = g.per_z();
-  // default: about four waves of one resident block per SM; long chunks
-  // amortise the two prologue planes of each chunk
-  int gz = (4 * 152 + per - 1) / per;
-  int zch = zch_req > 0 ? zch_req : (nv + gz - 1) / gz;
+  int zch = zch_req;
+  if (zch <= 0) {
+    // default: the z-chunk with the least modelled time: whole waves of
+    // `slots` resident blocks times the planes a block marches (its chunk
+    // plus about one plane's worth of prologue); longer chunks win ties
+    const int sl = slots > 0 ? slots : 2 * 152;
+    double best = 1e300;
+    for (int gz = 1; gz <= nv; ++gz) {
+      const int z = (nv + gz - 1) / gz;
+      if ((nv + z - 1) / z != gz) continue;  // the same chunk as a smaller gz
+      const double waves = (double)(((int64_t)per * gz + sl - 1) / sl);
+      const double cost = waves * (z + 1.0);
+      if (cost < best - 1e-9) {
+        best = cost;
+        zch = z;
+      }
+    }
+  }
   zch = std::max(zch, 1);
   zch = std::min(zch, nv);
   g.gz = (nv + zch - 1) / zch;
@@ -452,17 +503,18 @@ TileGrid edge_tiles(int n, int zch_req) {
 }
 
 template <typename T>
-cudaError_t launch_edge_sums(int n, const T* eta, T* hedge, cudaStream_t s) {
+cudaError_t launch_edge_records(int n, const T* eta, T* rec, cudaStream_t s) {
   const int64_t V = nverts(n);
-  return launch_k(edge_sum_kernel<T>, dim3((unsigned)((V + 255) / 256)), dim3(256), 0, s, n, eta, hedge);
+  return launch_k(edge_record_kernel<T>, dim3((unsigned)((V + 255) / 256)), dim3(256), 0, s, n, eta, rec);
 }
-template cudaError_t launch_edge_sums<double>(int, const double*, double*, cudaStream_t);
+template cudaError_t launch_edge_records<double>(int, const double*, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_stencil_edge(int mode, const LevelOp<T>& op, const StencilArgs<T>& a, cudaStream_t s, int zch_req) {
-  const TileGrid tg = edge_tiles(op.n, zch_req);
-  int dev = 0;
+  int dev = 0, sms = 152;
   KL(cudaGetDevice(&dev));
+  KL(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const TileGrid tg = edge_tiles(op.n, zch_req, edge_min_blocks<T, ST_RESID>() * sms);
   const dim3 grid((unsigned)tg.per_z(), (unsigned)tg.gz), block(ENT);
 #define AGCA_ELAUNCH(M)                                                                                     \
   do {                                                                                                      \
@@ -470,10 +522,10 @@ cudaError_t launch_stencil_edge(int mode, const LevelOp<T>& op, const StencilArg
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;                                                \
     if (!attr_set[dev]) {                                                                                   \
       KL(cudaFuncSetAttribute(stencil_edge_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                              (int)(edge_smem_elems<M>() * sizeof(T))));                                    \
+                              (int)(edge_smem_elems<T, M>() * sizeof(T))));                                    \
       attr_set[dev] = true;                                                                                 \
     }                                                                                                       \
-    KL(launch_k(stencil_edge_kernel<T, M>, grid, block, edge_smem_elems<M>() * sizeof(T), s, op, a, tg.zch,     \
+    KL(launch_k(stencil_edge_kernel<T, M>, grid, block, edge_smem_elems<T, M>() * sizeof(T), s, op, a, tg.zch,     \
                 tg.gxw));                                                                                   \
   } while (0)
   switch (mode) {
@@ -502,10 +554,10 @@ cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, 
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;                                                  \
     if (!attr_set[dev]) {                                                                                     \
       KL(cudaFuncSetAttribute(stencil_edge_batch_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                              (int)(edge_smem_elems<M>() * sizeof(T))));                                      \
+                              (int)(edge_smem_elems<T, M>() * sizeof(T))));                                      \
       attr_set[dev] = true;                                                                                   \
     }                                                                                                         \
-    KL(launch_k(stencil_edge_batch_kernel<T, M>, grid, block, edge_smem_elems<M>() * sizeof(T), s, tasks,     \
+    KL(launch_k(stencil_edge_batch_kernel<T, M>, grid, block, edge_smem_elems<T, M>() * sizeof(T), s, tasks,     \
                 ntasks, ntiles));                                                                             \
   } while (0)
   switch (mode) {
@@ -521,7 +573,11 @@ cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, 
 
 template cudaError_t launch_stencil_edge<double>(int, const LevelOp<double>&, const StencilArgs<double>&,
                                                   cudaStream_t, int);
+template cudaError_t launch_stencil_edge<float>(int, const LevelOp<float>&, const StencilArgs<float>&, cudaStream_t,
+                                                 int);
 template cudaError_t launch_stencil_edge_batch<double>(int, const StencilTask<double, double>*, int, int64_t,
                                                        cudaStream_t);
+template cudaError_t launch_stencil_edge_batch<float>(int, const StencilTask<float, float>*, int, int64_t,
+                                                      cudaStream_t);
 
 }  // namespace agca

@@ -44,8 +44,15 @@ def test_fgmres_matches_oracle(small, schur):
     x, its, rel = c.solve_fgmres(b, 1e-10, 2000, restart=50, schur=schur, z_iters=300)
     assert rel <= 1e-10
     assert abs(its - itso) <= 1, (its, itso)
+    xg = x.cpu().numpy()
+    # the oracle's own operator confirms the residual; the error against the
+    # direct solve is bounded by cond(K) times the residual (jump 1e4 here:
+    # about 4e-8 measured with the mass Schur block)
+    assert np.linalg.norm(bo - S.K(xg)) <= 1.01e-10 * np.linalg.norm(bo)
     xd = S.direct(bo)
-    assert np.abs(x.cpu().numpy() - xd).max() <= 1e-8 * np.abs(xd).max()
+    err = np.abs(xg - xd).max() / np.abs(xd).max()
+    print(f"\n4^3 FGMRES ({schur}) {its} iterations: error against the direct solve {err:.1e}")
+    assert err <= 1e-6
 
 
 def test_fgmres_restarts_and_agrees_with_minres():
