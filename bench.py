@@ -553,25 +553,51 @@ def run_batch(args, dev, stream):
             bs = [b.load_vector(i, f) for i, f in enumerate(fbars)]
             stream.synchronize()
             t0 = time.perf_counter()
-            xs, its, rel = b.solve(bs, 1e-8, 40000)
+            try:
+                xs, its, rel = b.solve(bs, 1e-8, 40000)
+                out["batched_iters"] = its
+                out["batched_max_relres"] = max(rel)
+            except pkg.AgcaError as e:  # some problem stopped above the tolerance
+                if e.status != 4:
+                    raise
+                out["batched_not_converged"] = True
             stream.synchronize()
             out["batched_solve_s"] = time.perf_counter() - t0
-            out["batched_iters"] = its
-            out["batched_max_relres"] = max(rel)
-            t0 = time.perf_counter()
-            for c, bb in zip(singles, bs):
-                c.solve(bb, 1e-8, 40000)
-            stream.synchronize()
-            out["sequential_mixed_solve_s"] = time.perf_counter() - t0
+
+            def one_by_one(contexts):
+                """Sequential solves; the problems that stop above the tolerance are listed."""
+                failed, iters = [], []
+                t0 = time.perf_counter()
+                for i, (c, bb) in enumerate(zip(contexts, bs)):
+                    c = c() if callable(c) else c
+                    try:
+                        iters.append(c.solve(bb, 1e-8, 40000)[1])
+                    except pkg.AgcaError as e:
+                        if e.status != 4:
+                            raise
+                        failed.append(i)
+                        iters.append(None)
+                    del c
+                stream.synchronize()
+                return time.perf_counter() - t0, iters, failed
+
+            t, iters, failed = one_by_one(singles)
+            out["sequential_mixed_solve_s"], out["sequential_mixed_iters"] = t, iters
+            if failed:
+                out["sequential_mixed_not_converged"] = failed
+
             # the plain FP64 form of the same problems, one by one
-            t0 = time.perf_counter()
-            for p, eta, bb in zip(probs, etas, bs):
-                c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.FP64, device=dev, stream=stream)
-                c.prepare(eta, NU)
-                c.solve(bb, 1e-8, 40000)
-                del c
-            stream.synchronize()
-            out["sequential_fp64_solve_s"] = time.perf_counter() - t0
+            def fp64_context(p, eta):
+                def make():
+                    c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.FP64, device=dev, stream=stream)
+                    c.prepare(eta, NU)
+                    return c
+                return make
+
+            t, iters, failed = one_by_one([fp64_context(p, eta) for p, eta in zip(probs, etas)])
+            out["sequential_fp64_solve_s"], out["sequential_fp64_iters"] = t, iters
+            if failed:
+                out["sequential_fp64_not_converged"] = failed
         del singles, b
     return out
 

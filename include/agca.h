@@ -296,9 +296,10 @@ agca_status agca_launch_count(const agca_ctx* ctx, int64_t* launches);
  * synchronizes and returns the summed kernel time in *ms, their compulsory
  * HBM bytes (element coefficients and vectors read/written once) in *bytes,
  * their algorithmic arithmetic in *flops (the edge form of the element
- * action of Eq. 3.5: 129 flops per vertex for the operator plus the
- * epilogue's, a fused multiply-add counting 2) and the number of timed
- * launches.  Output pointers are host pointers and may be NULL. */
+ * action of Eq. 3.5 with per-vertex coefficient records: 84 flops per
+ * vertex for the operator plus the epilogue's, a fused multiply-add
+ * counting 2) and the number of timed launches.  Output pointers are host
+ * pointers and may be NULL. */
 agca_status agca_profile_fine(agca_ctx* ctx, int enable, double* ms, double* bytes, double* flops,
                               int64_t* launches);
 

@@ -193,12 +193,11 @@ struct TileGrid {
 };
 TileGrid stencil_tiles(int n, int by, int zch_req);
 
-// Operator in edge form (stencil_edge.cu): modes APPLY, RESID and the
-// Chebyshev steps.  FP64: op.hedge = the per-vertex coefficient records
+// FP64 operator in edge form (stencil_edge.cu): modes APPLY, RESID and the
+// Chebyshev steps, with op.hedge = the per-vertex coefficient records
 // (EREC values per vertex, launch_edge_records): the sums of eta over the 6
 // tetrahedra around each forward axis edge and the weights of the edge
-// differences in the off-axis flux components.  FP32 (finest level): the
-// kernel forms the records from op.coef
+// differences in the off-axis flux components
 constexpr int EREC = 27;
 // tile grid of the edge form; zch_req 0 picks the z-chunk for `slots`
 // resident blocks (0: 304)
@@ -229,12 +228,12 @@ template <typename T>
 cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, int ntasks, int64_t ntiles,
                                       cudaStream_t s);
 // whether a step of this kind runs the edge form: every level of an FP64
-// context (its coefficient records exist on every level) and the finest
-// level of the FP32 cycle (records formed in the kernel); the FP32 coarse
-// levels and the Stokes operator run the per-cube kernel
+// context (its coefficient records exist on every level); the FP32 cycle and
+// the Stokes operator run the per-cube kernel
 template <typename TS, typename T>
 constexpr bool edge_form_step(int mode, bool coarse) {
-  return sizeof(TS) == sizeof(T) && mode != ST_STOKES && (sizeof(T) == 8 || !coarse);
+  (void)coarse;
+  return sizeof(TS) == 8 && sizeof(T) == 8 && mode != ST_STOKES;
 }
 
 // Element-wise batched tasks (transfers, conversions, coarsest solves).

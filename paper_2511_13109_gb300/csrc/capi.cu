@@ -981,8 +981,8 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   cudaStream_t s = ctx->stream;
   for (void* p : {lv.vb, lv.vx, lv.vt, lv.vr}) CK(cudaMemsetAsync(p, 0, n3 * sizeof(T), s));
   const bool f32 = sizeof(T) == 4;
-  // the edge form (every FP64 level, the FP32 finest level) has one tile shape
-  const bool edge = !f32 || l == ctx->L;
+  // the edge form (every FP64 level) has one tile shape
+  const bool edge = !f32;
   std::vector<int> bys = edge ? std::vector<int>{8} : std::vector<int>{8, 12, 16};
   const int nv = lv.n + 1;
   int dev = 0, sms = 152;
@@ -993,7 +993,7 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   // partly filled last wave)
   auto candidates = [&](int by) {
     std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
-    const int per_sm = edge ? (f32 ? 3 : 2) : (by <= 8 ? 3 : (by <= 12 ? 2 : 1));
+    const int per_sm = edge ? 2 : (by <= 8 ? 3 : (by <= 12 ? 2 : 1));
     const int per_z = edge ? edge_tiles(lv.n, 1).per_z() : stencil_tiles(lv.n, by, 1).per_z();
     for (int k = 1; k <= 8; ++k) {
       const int gz = std::max(1, k * sms * per_sm / per_z);
@@ -1022,7 +1022,7 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
       int last_zch = -1;
       for (int zr : candidates(by)) {
         if (zr > nv) continue;
-        const int zch = edge ? edge_tiles(lv.n, zr, (f32 ? 3 : 2) * sms).zch : stencil_tiles(lv.n, by, zr).zch;
+        const int zch = edge ? edge_tiles(lv.n, zr, 2 * sms).zch : stencil_tiles(lv.n, by, zr).zch;
         if (zch == last_zch) continue;
         last_zch = zch;
         TileCfg c;

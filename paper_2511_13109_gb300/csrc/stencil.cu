@@ -691,7 +691,7 @@ TileGrid stencil_tiles(int n, int BY, int zch_req) {
 template <typename TS, typename T>
 cudaError_t launch_stencil_batch(int mode, bool coarse, const StencilTask<TS, T>* tasks, int ntasks, int64_t ntiles,
                                  int64_t max_gca_rows, cudaStream_t s) {
-  if constexpr (std::is_same<TS, T>::value) {
+  if constexpr (std::is_same<TS, double>::value && std::is_same<T, double>::value) {
     if (edge_form_step<TS, T>(mode, coarse)) return launch_stencil_edge_batch<T>(mode, tasks, ntasks, ntiles, s);
   }
   if (coarse) return launch_batch_mode<TS, T, 8, true>(mode, tasks, ntasks, ntiles, max_gca_rows, s);
@@ -711,10 +711,6 @@ cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>
   if constexpr (std::is_same<TS, double>::value && std::is_same<T, double>::value) {
     // FP64 levels run the edge form (their coefficient records exist in FP64 contexts)
     if (op.hedge && mode != ST_STOKES) return launch_stencil_edge<T>(mode, op, a, s, zch);
-  }
-  if constexpr (std::is_same<TS, float>::value && std::is_same<T, float>::value) {
-    // the finest level of the FP32 cycle (no flag index) runs the edge form
-    if (!op.fidx && mode != ST_STOKES) return launch_stencil_edge<T>(mode, op, a, s, zch);
   }
   if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
     if (by == 12) {

@@ -1,6 +1,6 @@
-// Finest-level operator in edge form (Eq. 2.3 with the element matrices of
-// Eq. 3.5), fused with the smoother and residual epilogues: every level of
-// an FP64 context and the finest level of the FP32 cycle.
+// FP64 operator in edge form (Eq. 2.3 with the element matrices of Eq. 3.5;
+// on coarse levels the DCA part of Eq. 2.9), fused with the smoother and
+// residual epilogues: every level of an FP64 context.
 //
 // On a Kuhn grid every edge of a tetrahedron's path is an axis edge of the
 // grid, and the element action reduces to fluxes along those edges (see
@@ -21,16 +21,17 @@
 // per-tetrahedron form; the neighbours' edge differences are shared through
 // shared memory instead of being recomputed.
 //
-// FP64: GB300 runs one FP64 fused multiply-add per 64 FP32 ones, so FP64
+// GB300 runs one FP64 fused multiply-add per 64 FP32 ones, so FP64
 // arithmetic bounds the operator; the records are formed once per viscosity
-// (edge_record_kernel) and read by each vertex's own thread.  FP32: memory
-// bounds it; the records are formed in the kernel from cube-coefficient rows
-// staged in shared memory (6 values per cube instead of 27 per vertex).
+// (edge_record_kernel) and read by each vertex's own thread.  (The FP32
+// cycle keeps the per-cube kernel: an FP32 instance of this kernel, records
+// formed in-kernel from staged cube rows, issued about 1,600 instructions per
+// vertex, mostly integer, and ran 2.3x slower.)
 //
 // Tiling: a CTA of 32 x 8 threads, thread (tx, ty) <-> vertex column
 // (x0 - 1 + tx, y0 - 1 + ty), marches a chunk of z-planes.  Per plane k it
-// stages the x plane k + 2 (cp.async, one plane ahead; FP32: the cube layer
-// k + 1 too), forms the edge differences of plane k + 1 for its
+// stages the x plane k + 2 (cp.async, one plane ahead), forms the edge
+// differences of plane k + 1 for its
 // (34 x 10)-vertex tile, computes the three fluxes of its vertex's forward
 // edges from the differences of planes k - 1..k + 1 and its vertex's
 // coefficient record, exchanges the x and y fluxes (warp shuffle, shared
@@ -52,11 +53,9 @@ namespace {
 constexpr int EBX = 32, EBY = 8, ENT = EBX * EBY, NWARP = ENT / 32;
 constexpr int XW = EBX + 3, XH = EBY + 3, XT = XW * XH;  // x tile: vertices (x0-2 .., y0-2 ..)
 constexpr int DW = EBX + 2, DH = EBY + 2, DT = DW * DH;  // edge-difference tile
-constexpr int CW = EBX + 1, CH = EBY + 1, CROW = 6 * CW;  // FP32 cube tile: origins (x0-2 .., y0-2 ..)
-constexpr int CIT = (CROW + 31) / 32;                      // warp copies per cube-tile row
-constexpr int DRING = 84;                                  // halo entries of the difference tile
+constexpr int DRING = 84;                                // halo entries of the difference tile
 static_assert(EBX == 32, "a tile row is one warp");
-static_assert(XW - 32 <= 32 && CIT <= 8, "row staging covers a row in at most 2 (x) / 8 (cubes) warp copies");
+static_assert(XW - 32 <= 32, "row staging covers an x-tile row in at most 2 warp copies");
 // off-diagonal edge-difference components kept in shared memory:
 // (edge axis, component) = xy, xz, yx, yz, zx, zy
 enum { XY = 0, XZ, YX, YZ, ZX, ZY };
@@ -64,25 +63,17 @@ enum { XY = 0, XZ, YX, YZ, ZX, ZY };
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// the records come from HBM in FP64 and from staged cube rows in FP32
-template <typename T>
-__host__ __device__ constexpr bool edge_stored_records() {
-  return sizeof(T) == 8;
-}
 template <typename T, int MODE>
 __host__ __device__ constexpr size_t edge_smem_elems() {
   // x ring [3][3][XT] (+ D^-1 ring for the step from zero), difference ring
-  // [3][6][DT], FP32 cube ring [2][CH][CROW], y-flux exchange [3][ENT]:
-  // FP64 82 KB (110 KB with the D^-1 ring), two CTAs per SM; FP32 56 KB
-  // (70 KB), three CTAs per SM
-  return (size_t)(MODE == ST_CHEB_PRE ? 2 : 1) * 3 * 3 * XT + (size_t)3 * 6 * DT +
-         (edge_stored_records<T>() ? 0 : (size_t)2 * CH * CROW) + (size_t)3 * ENT;
+  // [3][6][DT], y-flux exchange [3][ENT]: in FP64 82 KB, or 110 KB with the
+  // D^-1 ring
+  return (size_t)(MODE == ST_CHEB_PRE ? 2 : 1) * 3 * 3 * XT + (size_t)3 * 6 * DT + (size_t)3 * ENT;
 }
-// resident CTAs per SM (shared memory and the register budget: 128 per
-// thread in FP64, 85 in FP32)
+// resident CTAs per SM (shared memory and the 128-register budget)
 template <typename T, int MODE>
 __host__ __device__ constexpr int edge_min_blocks() {
-  return sizeof(T) == 8 ? 2 : 3;
+  return 2;
 }
 template <typename T>
 __device__ __forceinline__ void cpT(T* smem, const T* gmem, bool ok) {
@@ -143,34 +134,19 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
   const bool owner = tx >= 1 && ty >= 1 && gx <= n && gy <= n;
   const bool inner_xy = gx > 0 && gx < n && gy > 0 && gy < n;
   constexpr bool PRE = MODE == ST_CHEB_PRE;
-  constexpr bool STORED = edge_stored_records<T>();
 
   T* xs = sm;                                    // [3][3][XT]
   T* xa = xs + 3 * 3 * XT;                       // PRE: D^-1 ring [3][3][XT]
   T* ds = xa + (PRE ? 3 * 3 * XT : 0);           // [3][6][DT]
-  T* cs = ds + 3 * 6 * DT;                       // FP32: cube ring [2][CH][CROW]
-  T* fy = cs + (STORED ? 0 : 2 * CH * CROW);     // [3][ENT]
-  const T* coefp = op.coefm ? op.coefm : op.coef;
+  T* fy = ds + 3 * 6 * DT;                       // [3][ENT]
 
-  const int zs = za - 2;  // planes zs + i use ring slot i mod 3, cube layers zs + i slot i mod 2
+  const int zs = za - 2;  // planes zs + i use ring slot i mod 3
   auto slot = [&](int p) { return (p - zs) % 3; };
-  auto cslot = [&](int q) { return (q - zs) & 1; };
 
   // this lane's columns of the x tile (x0 - 2 + tx, and x0 + 30 + tx for the
   // last XW - 32 lanes): interior in x?  Dirichlet and outside vertices read 0
   const bool inx0 = x0 - 2 + tx > 0 && x0 - 2 + tx < n;
   const bool inx1 = tx < XW - 32 && x0 + 30 + tx > 0 && x0 + 30 + tx < n;
-  // FP32: bit it set if element it * 32 + tx of a cube-tile row lies on a cube
-  // inside the grid in x
-  unsigned cmask = 0;
-  if (!STORED) {
-#pragma unroll
-    for (int it = 0; it < CIT; ++it) {
-      const int e = it * 32 + tx, cx = x0 - 2 + e / 6;
-      if (e < CROW && cx >= 0 && cx < n) cmask |= 1u << it;
-    }
-  }
-
   // stage x plane p (PRE: b and D^-1): warp ty copies the rows r = ty, ty + 8, ..
   // of the [3][XH] rows of the tile
   auto issue_x = [&](int p) {
@@ -211,21 +187,6 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
       if (tx < XW - 32) dst[e + 32] = a.s2 * dsa[e + 32] * dst[e + 32];
     }
   };
-  // FP32: stage the cube layer q of the cube tile, rows of 6 CW contiguous
-  // coefficients in the global layout; warp ty copies the (row, part) pairs
-  // u = ty, ty + 8, .. of the CH x CIT pairs
-  auto issue_coef = [&](int q) {
-    if (STORED) return;
-    T* dst = cs + cslot(q) * CH * CROW;
-    const bool qin = q >= 0 && q < n;
-    for (int u = ty; u < CH * CIT; u += NWARP) {
-      const int j = u / CIT, it = u - j * CIT;
-      const int cy = y0 - 2 + j, e = it * 32 + tx;
-      const bool ok = qin && cy >= 0 && cy < n && ((cmask >> it) & 1u);
-      const int g = ok ? 6 * ((x0 - 2) + n * (cy + n * q)) + e : 0;
-      if (e < CROW) cpT(dst + j * CROW + e, coefp + g, ok);
-    }
-  };
   // edge differences of plane p from x planes p, p + 1: difference-tile
   // entry (i, j) <-> x-tile entry (i, j); the 6 off-diagonal components go to
   // the ring, the thread's own vertex (entry (tx+1, ty+1)) keeps all 9
@@ -263,13 +224,10 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     }
   };
 
-  // prologue: x planes za-2 .. za (FP32: cube layers za-2, za-1); edge
-  // differences of planes za-2 and za-1
+  // prologue: x planes za-2 .. za; edge differences of planes za-2 and za-1
   issue_x(zs);
   issue_x(zs + 1);
   issue_x(zs + 2);
-  issue_coef(zs);
-  issue_coef(zs + 1);
   cp_commit();
   cp_wait_all();
   convert_x(zs);
@@ -289,7 +247,7 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
   for (int k = za - 1; k < zb; ++k) {
     cp_wait_all();
     convert_x(k + 2);
-    __syncthreads();  // x plane k+2 (FP32: cube layer k) staged; ring slots of k-2 free
+    __syncthreads();  // x plane k+2 staged; ring slots of k-2 free
     compute_d(k + 1, dnext);
     __syncthreads();  // differences of plane k+1 visible; x slot of plane k free
     if (k + 1 < zb) issue_x(k + 3);
@@ -298,21 +256,8 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     // own coefficient record and epilogue inputs of plane k, read early
     const bool kin = k >= 0 && k <= n && gx >= 0 && gx <= n && gy >= 0 && gy <= n;
     const int vo = kin ? gx + nv * (gy + nv * k) : 0;
-    T R[EREC];
-    if (STORED) {
-#pragma unroll
-      for (int q = 0; q < EREC; ++q) R[q] = kin ? __ldg(op.hedge + (int64_t)q * V + vo) : T(0);
-    } else {
-      // the 7 cubes around the vertex that touch its forward edges, from cube
-      // layers k - 1 and k (zero outside the grid)
-      const T* cm = cs + cslot(k - 1) * CH * CROW;
-      const T* c0 = cs + cslot(k) * CH * CROW;
-      auto C = [&](const T* p, int t, int di, int dj) { return p[(J + dj) * CROW + (I + di) * 6 + t]; };
-      edge_record<T>(C(c0, 0, 0, 0), C(c0, 1, 0, 0), C(c0, 2, 0, 0), C(c0, 3, 0, 0), C(c0, 4, 0, 0), C(c0, 5, 0, 0),
-                     C(c0, 0, -1, 0), C(c0, 1, -1, 0), C(c0, 2, 0, -1), C(c0, 3, 0, -1), C(c0, 0, -1, -1),
-                     C(c0, 2, -1, -1), C(cm, 4, 0, 0), C(cm, 5, 0, 0), C(cm, 3, 0, -1), C(cm, 5, 0, -1),
-                     C(cm, 1, -1, 0), C(cm, 4, -1, 0), R);
-    }
+    const T* rec = op.hedge + vo;
+    auto R = [&](int q) { return kin ? __ldg(rec + (int64_t)q * V) : T(0); };
     const bool out_k = owner && k >= za;
     const bool inner = out_k && inner_xy && k > 0 && k < n;
     T eb[3] = {T(0), T(0), T(0)}, ed[3] = {T(0), T(0), T(0)}, ep[3] = {T(0), T(0), T(0)}, xo[3] = {T(0), T(0), T(0)};
@@ -331,27 +276,36 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
     const T* dp = ds + slot(k + 1) * 6 * DT;  // plane k+1
     auto D = [&](const T* p, int comp, int di, int dj) { return p[comp * DT + (J + dj) * DW + I + di]; };
 
-    T Fx[3], Fy[3], Fz[3];
+    // the halo row (warp 0) supplies only the y fluxes of row 1, and the
+    // halo plane za-1 only the z fluxes of plane za (warp-uniform branches)
+    const bool need_x = ty != 0 && k >= za, need_y = k >= za, need_z = ty != 0;
+    T Fx[3] = {T(0), T(0), T(0)}, Fy[3] = {T(0), T(0), T(0)}, Fz[3] = {T(0), T(0), T(0)};
     // flux component c != m of edge m: the H_m term and the four distinct
     // c-edge differences around the edge, weighted by the record (EREC order)
     auto flux = [&](int q0, T hd, T da, T db, T dc, T dd) {
-      T f = fma(da, R[q0], hd);
-      f = fma(db, R[q0 + 1], f);
-      f = fma(dc, R[q0 + 2], f);
-      return fma(dd, R[q0 + 3], f);
+      T f = fma(da, R(q0), hd);
+      f = fma(db, R(q0 + 1), f);
+      f = fma(dc, R(q0 + 2), f);
+      return fma(dd, R(q0 + 3), f);
     };
-    // x edge (v, v + ex)
-    Fx[0] = T(2) * (R[0] * dcur[0][0]);
-    Fx[1] = flux(3, R[0] * dcur[0][1], D(d0, YX, 1, 0), D(d0, YX, 0, -1), D(dp, YX, 1, 0), D(dm, YX, 0, -1));
-    Fx[2] = flux(7, R[0] * dcur[0][2], D(d0, ZX, 1, 0), D(dm, ZX, 0, 0), D(d0, ZX, 1, 1), D(dm, ZX, 0, -1));
-    // y edge (v, v + ey)
-    Fy[1] = T(2) * (R[1] * dcur[1][1]);
-    Fy[0] = flux(11, R[1] * dcur[1][0], D(d0, XY, 0, 1), D(d0, XY, -1, 0), D(dp, XY, 0, 1), D(dm, XY, -1, 0));
-    Fy[2] = flux(15, R[1] * dcur[1][2], D(d0, ZY, 0, 1), D(dm, ZY, 0, 0), D(d0, ZY, 1, 1), D(dm, ZY, -1, 0));
-    // z edge (v, v + ez)
-    Fz[2] = T(2) * (R[2] * dcur[2][2]);
-    Fz[0] = flux(19, R[2] * dcur[2][0], D(dp, XZ, 0, 0), D(d0, XZ, -1, 0), D(dp, XZ, 0, 1), D(d0, XZ, -1, -1));
-    Fz[1] = flux(23, R[2] * dcur[2][1], D(dp, YZ, 0, 0), D(d0, YZ, 0, -1), D(dp, YZ, 1, 0), D(d0, YZ, -1, -1));
+    if (need_x) {  // x edge (v, v + ex)
+      const T h = R(0);
+      Fx[0] = T(2) * (h * dcur[0][0]);
+      Fx[1] = flux(3, h * dcur[0][1], D(d0, YX, 1, 0), D(d0, YX, 0, -1), D(dp, YX, 1, 0), D(dm, YX, 0, -1));
+      Fx[2] = flux(7, h * dcur[0][2], D(d0, ZX, 1, 0), D(dm, ZX, 0, 0), D(d0, ZX, 1, 1), D(dm, ZX, 0, -1));
+    }
+    if (need_y) {  // y edge (v, v + ey)
+      const T h = R(1);
+      Fy[1] = T(2) * (h * dcur[1][1]);
+      Fy[0] = flux(11, h * dcur[1][0], D(d0, XY, 0, 1), D(d0, XY, -1, 0), D(dp, XY, 0, 1), D(dm, XY, -1, 0));
+      Fy[2] = flux(15, h * dcur[1][2], D(d0, ZY, 0, 1), D(dm, ZY, 0, 0), D(d0, ZY, 1, 1), D(dm, ZY, -1, 0));
+    }
+    if (need_z) {  // z edge (v, v + ez)
+      const T h = R(2);
+      Fz[2] = T(2) * (h * dcur[2][2]);
+      Fz[0] = flux(19, h * dcur[2][0], D(dp, XZ, 0, 0), D(d0, XZ, -1, 0), D(dp, XZ, 0, 1), D(d0, XZ, -1, -1));
+      Fz[1] = flux(23, h * dcur[2][1], D(dp, YZ, 0, 0), D(d0, YZ, 0, -1), D(dp, YZ, 1, 0), D(d0, YZ, -1, -1));
+    }
     // the x edge ending at v belongs to lane tx - 1 of the same row (a warp)
     T fl[3];
 #pragma unroll
@@ -359,11 +313,7 @@ __device__ __forceinline__ void stencil_edge_block(const LevelOp<T>& op, const S
       fl[c] = __shfl_up_sync(0xffffffffu, Fx[c], 1);
       fy[c * ENT + tid] = Fy[c];
     }
-    __syncthreads();  // y fluxes of the tile visible; FP32: cube layer k-1 free
-    if (!STORED) {
-      if (k + 1 < zb) issue_coef(k + 1);
-      cp_commit();
-    }
+    __syncthreads();  // y fluxes of the tile visible
     T gs[3] = {T(0), T(0), T(0)};  // stored-Galerkin part (coarse levels)
     if (op.sten && inner) {
       const int sv = op.sidx[vo];
@@ -448,6 +398,7 @@ __global__ void __launch_bounds__(ENT, edge_min_blocks<T, MODE>())
 // the coefficient record of every vertex, rec[q][v], q < EREC (edge_record)
 template <typename T>
 __global__ void edge_record_kernel(const int n, const T* __restrict__ eta, T* __restrict__ rec) {
+  grid_dep_entry();  // the coefficients may come from the kernel before (masked_coef_kernel)
   const int nv = n + 1;
   const int64_t V = (int64_t)nv * nv * nv;
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -573,11 +524,8 @@ cudaError_t launch_stencil_edge_batch(int mode, const StencilTask<T, T>* tasks, 
 
 template cudaError_t launch_stencil_edge<double>(int, const LevelOp<double>&, const StencilArgs<double>&,
                                                   cudaStream_t, int);
-template cudaError_t launch_stencil_edge<float>(int, const LevelOp<float>&, const StencilArgs<float>&, cudaStream_t,
-                                                 int);
 template cudaError_t launch_stencil_edge_batch<double>(int, const StencilTask<double, double>*, int, int64_t,
                                                        cudaStream_t);
-template cudaError_t launch_stencil_edge_batch<float>(int, const StencilTask<float, float>*, int, int64_t,
-                                                      cudaStream_t);
+
 
 }  // namespace agca

@@ -112,11 +112,17 @@ def test_adjoint_full_size_finite_differences(prec):
     """The adjoint benchmark workload (64^3 pressure cubes, 8 spheres, jump
     1e4, observation from log-viscosity + N(0, 0.1^2)): the autograd gradient
     against central finite differences of the forward solve along seeded
-    directions, to 1e-5 relative.  Forward solves go to a 1e-10 relative
-    residual (the FP64 floor of this field at 64^3 is 4.4e-11), the adjoint
-    solve to 1e-9 (its right-hand side u - u_obs has its own floor), and the
-    fourth-order central difference takes eps = 1e-3: the forward solves'
-    errors enter it at about 1e-7 and the truncation at about 1e-12."""
+    directions.  Forward solves go to a 1e-10 relative residual (the FP64
+    floor of this field at 64^3 is 4.4e-11), the adjoint solve to 1e-9 (its
+    right-hand side u - u_obs has its own floor).  The fourth-order central
+    difference then resolves a directional derivative to about 1e-9
+    absolute: its noise (the solves' errors divided by eps, 1.3e-9 measured
+    at eps = 1e-3) and its truncation (eps^4, 4.8e-9 measured at eps = 1e-2)
+    balance near eps = 4e-3.  Each direction must agree to 1e-5 of the
+    larger of its own derivative and the root mean square over the
+    directions, so a direction whose derivative nearly cancels (|dJ| ~ 1e-5
+    against a typical 1e-3) is held to the finite difference's resolution;
+    the count of directions within 1e-5 of their own derivative is printed."""
     from synth import adjoint_problem
 
     N = 64
@@ -138,12 +144,16 @@ def test_adjoint_full_size_finite_differences(prec):
     (0.5 * torch.sum((u - u_obs) ** 2)).backward()
     g = th.grad.clone()
     assert torch.isfinite(g).all()
-    eps = 1e-3
-    worst = 0.0
+    eps = 4e-3
+    pairs = []
     for k in range(FULL_DIRECTIONS[prec]):
         d = torch.from_numpy(np.random.default_rng(200 + k).normal(size=theta.numel())).to(DEV)
-        fd = _fd4(J, theta, d, eps)
-        ad = float(torch.dot(g, d))
-        worst = max(worst, abs(fd - ad) / abs(fd))
-        assert abs(fd - ad) <= 1e-5 * abs(fd), (k, fd, ad)
-    print(f"\n64^3 adjoint ({prec}): {FULL_DIRECTIONS[prec]} directions, worst relative FD difference {worst:.2e}")
+        pairs.append((_fd4(J, theta, d, eps), float(torch.dot(g, d))))
+    fds = np.array([f for f, _ in pairs])
+    rms = float(np.sqrt(np.mean(fds ** 2)))
+    strict = sum(abs(f - a) <= 1e-5 * abs(f) for f, a in pairs)
+    worst = max(abs(f - a) / max(abs(f), rms) for f, a in pairs)
+    print(f"\n64^3 adjoint ({prec}): {len(pairs)} directions, rms derivative {rms:.3e}, worst difference "
+          f"{worst:.2e} of max(|dJ|, rms); {strict} of {len(pairs)} within 1e-5 of their own derivative")
+    for k, (f, a) in enumerate(pairs):
+        assert abs(f - a) <= 1e-5 * max(abs(f), rms), (k, f, a, rms)
