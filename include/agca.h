@@ -212,9 +212,12 @@ agca_status agca_solve(agca_ctx* ctx, const double* b_dev, double* x_dev, double
  * at most rtol ||b|| (Eq. 4.3).  schur: 0 = S~^-1 the mean-free lumped 1/eta
  * pressure mass; 1 = the diag(A)-BFBT of Eq. 4.2, S~^-1 = Z^-1 (B W^-1 A
  * W^-1 B^T) Z^-1 with W = diag(A), Z = B W^-1 B^T assembled at each call
- * on the pressure grid (App. B; 125 matrix-free applies to colour
- * indicators give its 5x5x5 stencils) and Z^-1 by z_iters steps of
- * Jacobi-preconditioned conjugate gradients on the mean-free pressures.
+ * on the pressure grid (App. B; Z couples pressure vertices whose offset is
+ * a sum of two Kuhn offsets, 65 in all, and 125 matrix-free applies to
+ * colour indicators give those stencils) and Z^-1 by z_iters steps of
+ * Jacobi-preconditioned conjugate gradients on the mean-free pressures (one
+ * cooperative launch per solve; the device must support cooperative
+ * launches, else the call fails with AGCA_ECUDA).
  * work_dev: caller-owned device memory of agca_fgmres_workspace_size bytes
  * (256-byte aligned; holds the 2 restart + 1 Krylov vectors and Z).  x is
  * overwritten (initial guess 0; pressure returned mean-free).  *iters,

@@ -334,21 +334,22 @@ cudaError_t launch_krylov_batch(int op, const KTask* tasks, int ntasks, int64_t 
                                 cudaStream_t s);
 cudaError_t launch_mask_boundary(int n, double* x, cudaStream_t s);
 // FGMRES pieces: out[i] = w . V_i (i < nvec, V_i = V + i ld); w += sign sum_i coef[i] V_i;
-// y = a * s or a / s (s on the device); conjugate-gradient updates on device scalars
-// sc[0] = rho, sc[1] = p.q, sc[2] = rho_new
+// y = a * s or a / s (s on the device)
 cudaError_t launch_block_dot(int nvec, const double* V, int64_t ld, const double* w, int64_t n, double* partials,
                              double* out, cudaStream_t s);
 cudaError_t launch_block_axpy(int nvec, const double* V, int64_t ld, const double* coef, double sign, double* w,
                               int64_t n, cudaStream_t s);
 cudaError_t launch_scale(int64_t n, double* y, const double* a, const double* s_dev, bool recip, cudaStream_t s);
-cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* sc,
-                             cudaStream_t s);
-cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* sc, cudaStream_t s);
-// assembled Z = B W^-1 B^T as per-vertex 5x5x5 stencils on the pressure grid
-// (zs: [V_p][125], offset (di, dj, dk) at (di+2) + 5 (dj+2) + 25 (dk+2))
+// assembled Z = B W^-1 B^T on the pressure grid as per-vertex stencils over
+// the ZSTENCIL offsets that are sums of two Kuhn offsets, SoA [ZSTENCIL][V]
+constexpr int ZSTENCIL = 65;
 cudaError_t launch_colour5(int np, int colour, double* e, cudaStream_t s);
 cudaError_t launch_scatter_zrow(int np, int colour, const double* y, double* zs, cudaStream_t s);
-cudaError_t launch_zstencil(int np, const double* zs, const double* p, double* y, cudaStream_t s);
+// x = Z^-1 r by `iters` Jacobi-PCG steps from 0 in one cooperative launch (r
+// mean-free on entry, overwritten; x not projected); partials: partials_cap
+// doubles of scratch
+cudaError_t launch_zcg(int np, const double* zs, const double* dinv, double* x, double* r, double* p, double* q,
+                       double* partials, int64_t partials_cap, int iters, cudaStream_t s);
 cudaError_t launch_zdiag_inv(int np, const double* zs, double* dinv, cudaStream_t s);
 cudaError_t launch_sensitivity(int n, const double* eta, const double* lam, const double* u, double* g,
                                cudaStream_t s);

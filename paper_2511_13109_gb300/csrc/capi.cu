@@ -732,6 +732,7 @@ agca_status solve_impl(agca_ctx* ctx, const double* b_in, double* x, double rtol
 // by Givens rotations on the host.
 struct FgmresWork {
   double *V, *Z, *w, *t1, *t2, *partials, *hbuf, *ycoef, *zdinv, *cx, *cr, *cz, *cp, *cq, *m, *sc, *zsten;
+  int64_t npartials;
   size_t need;
 };
 
@@ -744,7 +745,8 @@ FgmresWork fgmres_layout(const agca_ctx* ctx, int restart, char* base) {
   w.w = cv.take<double>(nt);
   w.t1 = cv.take<double>(nt);
   w.t2 = cv.take<double>(nt);
-  w.partials = cv.take<double>((int64_t)(restart + 1) * dot_blocks());
+  w.npartials = (int64_t)(restart + 1) * dot_blocks();
+  w.partials = cv.take<double>(w.npartials);
   w.hbuf = cv.take<double>(2 * (restart + 1) + 8);
   w.ycoef = cv.take<double>(restart + 1);
   w.zdinv = cv.take<double>(np);
@@ -755,7 +757,7 @@ FgmresWork fgmres_layout(const agca_ctx* ctx, int restart, char* base) {
   w.cq = cv.take<double>(np);
   w.m = cv.take<double>(np);
   w.sc = cv.take<double>(8);
-  w.zsten = cv.take<double>(np * 125);
+  w.zsten = cv.take<double>(np * ZSTENCIL);
   w.need = (cv.off + kAlign - 1) / kAlign * kAlign;
   return w;
 }
@@ -783,24 +785,11 @@ agca_status mean_free(agca_ctx* ctx, double* y) {
 
 // x = Z^-1 rhs on the mean-free pressures: iters steps of Jacobi-preconditioned CG from 0
 agca_status z_solve(agca_ctx* ctx, const FgmresWork& W, const double* rhs, double* x, int iters) {
-  const int64_t np = ctx->Vp, n3 = 3 * ctx->lev[ctx->L].V;
+  const int64_t np = ctx->Vp;
   cudaStream_t s = ctx->stream;
   LK(1, launch_vec_op(VOP_COPY, np, W.cr, rhs, nullptr, nullptr, nullptr, s));
   CKS(mean_free(ctx, W.cr));
-  LK(1, launch_vec_op(VOP_ZERO, np, x, nullptr, nullptr, nullptr, nullptr, s));
-  LK(1, launch_vec_op(VOP_MUL, np, W.cz, W.cr, W.zdinv, nullptr, nullptr, s));
-  CKS(mean_free(ctx, W.cz));
-  LK(1, launch_vec_op(VOP_COPY, np, W.cp, W.cz, nullptr, nullptr, nullptr, s));
-  CKS(dot1(ctx, W.cr, W.cz, np, W.sc + 0));
-  for (int it = 0; it < iters; ++it) {
-    LK(1, launch_zstencil(ctx->N, W.zsten, W.cp, W.cq, s));
-    CKS(dot1(ctx, W.cp, W.cq, np, W.sc + 1));
-    LK(1, launch_cg_update(np, x, W.cr, W.cp, W.cq, W.sc, s));
-    LK(1, launch_vec_op(VOP_MUL, np, W.cz, W.cr, W.zdinv, nullptr, nullptr, s));
-    CKS(mean_free(ctx, W.cz));
-    CKS(dot1(ctx, W.cr, W.cz, np, W.sc + 2));
-    LK(2, launch_cg_direction(np, W.cp, W.cz, W.sc, s));
-  }
+  LK(1, launch_zcg(ctx->N, W.zsten, W.zdinv, x, W.cr, W.cp, W.cq, W.partials, W.npartials, iters, s));
   CKS(mean_free(ctx, x));
   return AGCA_OK;
 }

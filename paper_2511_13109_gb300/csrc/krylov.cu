@@ -1,8 +1,13 @@
 // Krylov-side kernels (FP64): deterministic dot products, the preconditioned
 // MINRES recurrence of Remark 6 with its scalars kept on the device, the
-// pressure block of the block-diagonal preconditioner, the load vector and
-// the element sensitivities of the adjoint gradient.
+// pressure block of the block-diagonal preconditioner, the load vector, the
+// element sensitivities of the adjoint gradient, and FGMRES's pieces (block
+// Gram-Schmidt, the assembled Z of the BFBT Schur block and its
+// conjugate-gradient solve).
 #include <math.h>
+
+#include <algorithm>
+#include <cooperative_groups.h>
 
 #include "agca_internal.cuh"
 
@@ -320,33 +325,46 @@ __global__ void scale_kernel(int64_t n, double* __restrict__ y, const double* __
 
 // conjugate-gradient vector updates on the device scalars sc: x += alpha p,
 // r -= alpha q with alpha = sc[0] / sc[1]; p = z + beta p with beta = sc[2] / sc[0]
-__global__ void cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
-                                 const double* __restrict__ p, const double* __restrict__ q,
-                                 const double* __restrict__ sc) {
-  grid_dep_entry();
-  const double alpha = sc[1] != 0.0 ? sc[0] / sc[1] : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    r[i] = fma(-alpha, q[i], r[i]);
-  }
-}
-__global__ void cg_direction_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
-                                    double* __restrict__ sc) {
-  grid_dep_entry();
-  const double beta = sc[0] != 0.0 ? sc[2] / sc[0] : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
-}
-__global__ void cg_shift_kernel(double* sc) {
-  grid_dep_entry();
-  if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = sc[2];  // rho <- rho_new
-}
-
-// Assembled Z = B W^-1 B^T on the pressure grid (np cubes per axis) as
-// per-vertex 5x5x5 stencils: Z couples pressure vertices at most 2 cells
-// apart, so applying Z to the indicator of colour (a, b, c) (vertices with
+// Assembled Z = B W^-1 B^T on the pressure grid (np cubes per axis).  A
+// pressure hat and a velocity hat overlap only where their Kuhn
+// neighbourhoods meet, so Z couples pressure vertices whose offset is a sum
+// of two Kuhn offsets: 65 offsets in [-2, 2]^3.  Z is kept as per-vertex
+// stencils over those offsets, SoA zs[s * V + v] (slot s in the order
+// below).  Applying Z to the indicator of colour (a, b, c) (vertices with
 // coordinates = (a, b, c) mod 5) yields, at every vertex l, the one entry
-// Z[l][k] of the colour vertex k within distance 2 of l.
+// Z[l][k] of the colour vertex k within distance 2 of l, so 125 colours
+// recover every stencil.
+struct ZPattern {
+  signed char d[65][3];   // offsets (dx, dy, dz), ascending in (dz, dy, dx)
+  signed char slot[125];  // (dx + 2) + 5 (dy + 2) + 25 (dz + 2) -> slot, or -1
+  int n, centre;
+};
+constexpr ZPattern make_zpattern() {
+  ZPattern p{};
+  for (int q = 0; q < 125; ++q) p.slot[q] = -1;
+  for (int dz = -2; dz <= 2; ++dz)
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        bool in = false;
+        for (int a = 0; a < 15; ++a)
+          for (int b = 0; b < 15; ++b)
+            in = in || (kuhn_offset_comp(a, 0) + kuhn_offset_comp(b, 0) == dx &&
+                        kuhn_offset_comp(a, 1) + kuhn_offset_comp(b, 1) == dy &&
+                        kuhn_offset_comp(a, 2) + kuhn_offset_comp(b, 2) == dz);
+        if (!in) continue;
+        if (dx == 0 && dy == 0 && dz == 0) p.centre = p.n;
+        p.d[p.n][0] = (signed char)dx;
+        p.d[p.n][1] = (signed char)dy;
+        p.d[p.n][2] = (signed char)dz;
+        p.slot[(dx + 2) + 5 * (dy + 2) + 25 * (dz + 2)] = (signed char)p.n;
+        ++p.n;
+      }
+  return p;
+}
+constexpr ZPattern kZPattern = make_zpattern();
+static_assert(kZPattern.n == ZSTENCIL, "sums of two Kuhn offsets: 65 distinct offsets");
+__constant__ ZPattern c_zpat = make_zpattern();
+
 __global__ void colour5_kernel(int np, int colour, double* __restrict__ e) {
   grid_dep_entry();
   const int nv = np + 1;
@@ -367,43 +385,106 @@ __global__ void scatter_zrow_kernel(int np, int colour, const double* __restrict
   if (v >= V) return;
   const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
   const int di = offset5(i, colour % 5), dj = offset5(j, (colour / 5) % 5), dk = offset5(k, colour / 25);
-  zs[v * 125 + (di + 2) + 5 * (dj + 2) + 25 * (dk + 2)] = y[v];
-}
-// y = Z p from the assembled stencils (neighbours outside the grid contribute nothing)
-__global__ void zstencil_kernel(int np, const double* __restrict__ zs, const double* __restrict__ p,
-                                double* __restrict__ y) {
-  grid_dep_entry();
-  const int nv = np + 1;
-  const int64_t V = (int64_t)nv * nv * nv;
-  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
-  const double* row = zs + v * 125;
-  double acc = 0.0;
-  for (int dk = -2; dk <= 2; ++dk) {
-    const int kk = k + dk;
-    if (kk < 0 || kk > np) continue;
-    for (int dj = -2; dj <= 2; ++dj) {
-      const int jj = j + dj;
-      if (jj < 0 || jj > np) continue;
-#pragma unroll
-      for (int di = -2; di <= 2; ++di) {
-        const int ii = i + di;
-        if (ii < 0 || ii > np) continue;
-        acc = fma(row[(di + 2) + 5 * (dj + 2) + 25 * (dk + 2)], __ldg(p + ii + (int64_t)nv * (jj + (int64_t)nv * kk)),
-                  acc);
-      }
-    }
-  }
-  y[v] = acc;
+  const int s = c_zpat.slot[(di + 2) + 5 * (dj + 2) + 25 * (dk + 2)];
+  if (s >= 0) zs[s * V + v] = y[v];  // Z vanishes at the other offsets
 }
 // inverse diagonal of the assembled Z (0 where it is not positive)
 __global__ void zdiag_inv_kernel(int64_t V, const double* __restrict__ zs, double* __restrict__ dinv) {
   grid_dep_entry();
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= V) return;
-  const double d = zs[v * 125 + 62];
+  const double d = zs[kZPattern.centre * V + v];
   dinv[v] = d > 0.0 ? 1.0 / d : 0.0;
+}
+
+// (Z p)_v from the stencils (neighbours outside the grid contribute nothing)
+__device__ __forceinline__ double zrow(const double* __restrict__ zs, const double* __restrict__ p, int64_t V, int nv,
+                                       int64_t v) {
+  const int i = (int)(v % nv), j = (int)((v / nv) % nv), k = (int)(v / ((int64_t)nv * nv));
+  double acc = 0.0;
+#pragma unroll 5
+  for (int s = 0; s < ZSTENCIL; ++s) {
+    const int ii = i + c_zpat.d[s][0], jj = j + c_zpat.d[s][1], kk = k + c_zpat.d[s][2];
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= nv || jj >= nv || kk >= nv) continue;
+    acc = fma(zs[s * V + v], p[ii + (int64_t)nv * (jj + (int64_t)nv * kk)], acc);
+  }
+  return acc;
+}
+
+// Sum of one value per thread over the whole grid: block sums into
+// partials[blockIdx], a grid barrier, then every block adds the partials in
+// index order (the same bits in every block and every run)
+__device__ double zcg_grid_sum(cooperative_groups::grid_group& grid, double v, double* partials, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+  }
+  grid.sync();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += partials[b];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  const double total = red[32];
+  __syncthreads();  // red is reused by the next sum
+  return total;
+}
+
+// x = Z^-1 r by `iters` steps of Jacobi-preconditioned conjugate gradients
+// from x = 0, in one cooperative launch (grid barriers between the phases
+// of a step).  r (mean-free) is overwritten by the residual.  The iterates
+// are not projected: r stays mean-free because Z annihilates constants, so
+// the constant parts p and x pick up change no inner product, and the
+// caller projects x once at the end.  partials: 2 gridDim.x doubles.
+__global__ void __launch_bounds__(256) zcg_kernel(int np, const double* __restrict__ zs, const double* __restrict__ dinv,
+                                                  double* __restrict__ x, double* __restrict__ r,
+                                                  double* __restrict__ p, double* __restrict__ q,
+                                                  double* __restrict__ partials, int iters) {
+  grid_dep_entry();
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ double red[33];
+  const int nv = np + 1;
+  const int64_t V = (int64_t)nv * nv * nv;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  double* part[2] = {partials, partials + gridDim.x};  // alternate: consecutive uses are a barrier apart
+  double loc = 0.0;
+  for (int64_t v = t0; v < V; v += st) {
+    const double z = dinv[v] * r[v];
+    x[v] = 0.0;
+    p[v] = z;
+    loc = fma(r[v], z, loc);
+  }
+  double rho = zcg_grid_sum(grid, loc, part[0], red);
+  for (int it = 0; it < iters; ++it) {
+    grid.sync();  // p complete
+    loc = 0.0;
+    for (int64_t v = t0; v < V; v += st) {
+      const double qv = zrow(zs, p, V, nv, v);
+      q[v] = qv;
+      loc = fma(p[v], qv, loc);
+    }
+    const double pq = zcg_grid_sum(grid, loc, part[1], red);
+    const double alpha = pq != 0.0 ? rho / pq : 0.0;
+    loc = 0.0;
+    for (int64_t v = t0; v < V; v += st) {
+      x[v] = fma(alpha, p[v], x[v]);
+      const double rv = fma(-alpha, q[v], r[v]);
+      r[v] = rv;
+      loc = fma(rv, dinv[v] * rv, loc);
+    }
+    const double rho_new = zcg_grid_sum(grid, loc, part[0], red);
+    const double beta = rho != 0.0 ? rho_new / rho : 0.0;
+    rho = rho_new;
+    for (int64_t v = t0; v < V; v += st) p[v] = fma(beta, p[v], dinv[v] * r[v]);
+  }
 }
 
 }  // namespace
@@ -467,18 +548,6 @@ cudaError_t launch_scale(int64_t n, double* y, const double* a, const double* s_
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* sc,
-                             cudaStream_t s) {
-  KL(launch_k(cg_update_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, x, r, p, q, sc));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cg_direction(int64_t n, double* p, const double* z, double* sc, cudaStream_t s) {
-  KL(launch_k(cg_direction_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, p, z, sc));
-  KL(launch_k(cg_shift_kernel, dim3(1), dim3(32), 0, s, sc));
-  return cudaGetLastError();
-}
-
 cudaError_t launch_colour5(int np, int colour, double* e, cudaStream_t s) {
   KL(launch_k(colour5_kernel, dim3(blocks_for(nverts(np), 256)), dim3(256), 0, s, np, colour, e));
   return cudaGetLastError();
@@ -489,8 +558,25 @@ cudaError_t launch_scatter_zrow(int np, int colour, const double* y, double* zs,
   return cudaGetLastError();
 }
 
-cudaError_t launch_zstencil(int np, const double* zs, const double* p, double* y, cudaStream_t s) {
-  KL(launch_k(zstencil_kernel, dim3(blocks_for(nverts(np), 128)), dim3(128), 0, s, np, zs, p, y));
+cudaError_t launch_zcg(int np, const double* zs, const double* dinv, double* x, double* r, double* p, double* q,
+                       double* partials, int64_t partials_cap, int iters, cudaStream_t s) {
+  int dev = 0, sms = 152, per = 0, coop = 0;
+  KL(cudaGetDevice(&dev));
+  KL(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  KL(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return cudaErrorNotSupported;
+  KL(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, zcg_kernel, 256, 0));
+  // every block resident (a cooperative launch fails rather than waits
+  // otherwise); two per SM keep the per-step partial sums short
+  int64_t blocks = std::min<int64_t>((int64_t)std::min(per, 2) * sms, blocks_for(nverts(np), 256));
+  blocks = std::max<int64_t>(blocks, 1);
+  if (2 * blocks > partials_cap) return cudaErrorInvalidValue;
+  int np_ = np, iters_ = iters;
+  const double* zs_ = zs;
+  const double* dinv_ = dinv;
+  double *x_ = x, *r_ = r, *p_ = p, *q_ = q, *part_ = partials;
+  void* args[] = {&np_, &zs_, &dinv_, &x_, &r_, &p_, &q_, &part_, &iters_};
+  KL(cudaLaunchCooperativeKernel((const void*)zcg_kernel, dim3((unsigned)blocks), dim3(256), args, 0, s));
   return cudaGetLastError();
 }
 

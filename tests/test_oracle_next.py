@@ -193,6 +193,38 @@ def test_fgmres_vcycle_bfbt_matches_direct_solve(stokes_small):
     assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
 
 
+def test_z_couples_pressure_vertices_two_kuhn_offsets_apart():
+    """Z = B W^-1 B^T (the BFBT operator of Eq. 4.2) couples pressure vertex
+    i with j exactly when j - i is a sum of two Kuhn offsets (a pressure hat
+    and a velocity hat overlap only inside one pressure cell): 65 distinct
+    offsets in [-2, 2]^3, every one of them present at an interior vertex, so
+    per-vertex stencils over those 65 offsets hold Z, and mod-5 colour
+    probing separates them."""
+    from oracle import stokes as ostokes
+    from oracle.fgmres import BlockTriangular
+    from synth import sphere_sinkers
+
+    N = 6
+    p = sphere_sinkers(N, 2, 0.2, 0.05, 1e3, seed=9)
+    S = ostokes.Stokes(agca.Hierarchy(N, 2, p.eta, 10.0))
+    Z = BlockTriangular(S).Z.tocoo()
+    nv = N + 1
+    tol = 1e-13 * np.abs(Z.data).max()
+    ijk = lambda v: np.stack([v % nv, (v // nv) % nv, v // (nv * nv)], axis=-1)
+    keep = np.abs(Z.data) > tol
+    d = ijk(Z.col[keep]) - ijk(Z.row[keep])
+    offsets = set(map(tuple, d))
+    kuhn = [(0, 0, 0)] + [s * np.array(e) for e in ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1),
+                                                      (0, 1, 1), (1, 1, 1)) for s in (1, -1)]
+    pairs = {tuple(np.add(a, b)) for a in kuhn for b in kuhn}
+    assert len(pairs) == 65
+    assert offsets == pairs
+    # the centre vertex (3, 3, 3) couples with all 65
+    c = 3 + nv * (3 + nv * 3)
+    assert len(set(map(tuple, d[Z.row[keep] == c]))) == 65
+    assert np.abs(d).max() <= 2
+
+
 # ---- stencil storage of the coarse operators (Remark 5) ----
 def test_agca_rows_fit_the_15_point_kuhn_stencil():
     """Every level's AGCA operator, with DCA and stored Galerkin elements
