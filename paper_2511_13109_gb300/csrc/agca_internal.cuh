@@ -158,6 +158,10 @@ cudaError_t launch_k(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, 
 
 // ---------------------------------------------------------------- launchers
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_CHEB_FIRST = 2, ST_CHEB_STEP = 3, ST_CHEB_PRE = 4, ST_STOKES = 5 };
+// internal (FP64 contexts, not tunable): the pressure coupling of the Stokes
+// operator added to a.b = A u from the edge form, out = a.b - B_f^T q,
+// out2 = B_f u
+constexpr int ST_STOKES_B = 6;
 
 template <typename T>
 struct StencilArgs {

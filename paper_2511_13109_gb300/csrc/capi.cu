@@ -533,7 +533,18 @@ agca_status stokes_impl(agca_ctx* ctx, const double* x, double* y) {
   a.q = ctx->qfine;
   a.out = y;
   a.out2 = ctx->sfine;
-  LK(1, launch_stencil<double, TC>(ST_STOKES, level_op<TC>(ctx, L), a, ctx->stream));
+  if (std::is_same<TC, double>::value && lf.hedge) {
+    // FP64 context: the viscous block in edge form (A u into y), then the
+    // pressure coupling per cube added to it (y = A u - B_f^T q, B_f u)
+    StencilArgs<double> e{};
+    e.x = x;
+    e.out = y;
+    LK(1, launch_stencil<double, double>(ST_APPLY, op64(ctx, L), e, ctx->stream));
+    a.b = y;
+    LK(1, launch_stencil<double, double>(ST_STOKES_B, op64(ctx, L), a, ctx->stream));
+  } else {
+    LK(1, launch_stencil<double, TC>(ST_STOKES, level_op<TC>(ctx, L), a, ctx->stream));
+  }
   LK(1, launch_restrict<double>(lf.n, 1, false, -1.0, ctx->sfine, y + n3, ctx->stream));
   return AGCA_OK;
 }

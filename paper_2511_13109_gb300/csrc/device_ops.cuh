@@ -109,6 +109,36 @@ __device__ __forceinline__ void cube_stokes(const T (&Xl)[4][4], const T (&Xh)[4
   }
 }
 
+// The pressure coupling of cube_stokes alone (the viscous part comes from
+// the edge form): per tetrahedron -(h^2/6) qbar along the m-component of its
+// path edges and (|T|/4) div u at its corners, in component 3
+template <typename T>
+__device__ __forceinline__ void cube_stokes_b(const T (&Xl)[4][4], const T (&Xh)[4][4], const T hq, T (&Y)[8][4]) {
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    T qsum = T(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int q = tet_corner(t, a);
+      qsum += (q & 4) ? Xh[q & 3][3] : Xl[q & 3][3];
+    }
+    const T pq = T(0.25) * hq * qsum;  // (h^2/6) qbar
+    T tr = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int qa = tet_corner(t, k), qb = tet_corner(t, k + 1), m = perm(t, k);
+      const T xb = (qb & 4) ? Xh[qb & 3][m] : Xl[qb & 3][m];
+      const T xa = (qa & 4) ? Xh[qa & 3][m] : Xl[qa & 3][m];
+      tr += xb - xa;  // G[m][m]
+      Y[qb][m] -= pq;
+      Y[qa][m] += pq;
+    }
+    const T dv = T(0.25) * hq * tr;  // (|T|/4) div u
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Y[tet_corner(t, a)][3] += dv;
+  }
+}
+
 // Flagged elements of a coarse level: y_e = s_e A_e x_e (Eq. 2.9, stored
 // Galerkin part), one thread per (element, row), written to op.ye for the
 // stencil kernel to scatter.  x follows the stencil's input convention
@@ -186,6 +216,7 @@ template <int MODE, typename TS>
 __device__ __forceinline__ TS stencil_epilogue(const TS xo, const TS y, const TS eb, const TS ed, const TS ep,
                                                const TS s0, const TS s1) {
   if (MODE == ST_APPLY || MODE == ST_STOKES) return y;
+  if (MODE == ST_STOKES_B) return eb + y;
   if (MODE == ST_RESID) return eb - y;
   if (MODE == ST_CHEB_FIRST) return xo + s0 * ed * (eb - y);
   if (MODE == ST_CHEB_STEP) return xo + s0 * (xo - ep) + s1 * ed * (eb - y);

@@ -45,7 +45,7 @@ __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1
 
 template <int MODE, typename TS>
 __host__ __device__ constexpr int stencil_tile_fields() {
-  return MODE == ST_CHEB_PRE ? 9 : (MODE == ST_STOKES ? 4 : 3);
+  return MODE == ST_CHEB_PRE ? 9 : ((MODE == ST_STOKES || MODE == ST_STOKES_B) ? 4 : 3);
 }
 
 // FP32 tiles keep the operator input of a vertex as one float4 (its 3 or 4
@@ -82,7 +82,7 @@ __host__ __device__ constexpr bool stencil_converts() {
 }
 template <typename TS, typename T, int BX, int BY, int MODE>
 __host__ __device__ constexpr size_t stencil_smem_bytes() {
-  constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;
+  constexpr int NC = (MODE == ST_STOKES || MODE == ST_STOKES_B) ? 4 : 3;
   return stencil_tile_bytes<TS, BX, BY, MODE>() + (size_t)2 * BX * BY * 6 * sizeof(T) +
          (size_t)2 * (stencil_aos<TS>() ? 4 : NC) * BX * BY * sizeof(T) +
          (stencil_converts<TS, T, MODE>() ? (size_t)3 * NC * (BX + 1) * (BY + 1) * sizeof(T) : 0);
@@ -99,7 +99,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
                                               const int x0, const int y0, const int bz, const int tx, const int ty,
                                               unsigned char* __restrict__ smem_raw) {
   static_assert(BX == 32 || BX == 8, "a tile row is a whole warp or a quarter of one");
-  constexpr int NC = (MODE == ST_STOKES) ? 4 : 3;  // combined fields: velocity (+ divergence)
+  constexpr int NC = (MODE == ST_STOKES || MODE == ST_STOKES_B) ? 4 : 3;  // combined fields: velocity (+ divergence)
   constexpr int NF = stencil_tile_fields<MODE, TS>();
   constexpr int TW = BX + 1, TSZ = (BX + 1) * (BY + 1), NT = BX * BY;
   constexpr int NSLOT = (TSZ + NT - 1) / NT;
@@ -167,7 +167,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
           cp_async(AOS ? dst + 4 * idx + c : dst + c * TSZ + idx, a.x + (c * V + v), sizeof(TS), in);
         }
       }
-      if (MODE == ST_STOKES) {  // fine-grid pressure q = P p lives on every vertex
+      if (MODE == ST_STOKES || MODE == ST_STOKES_B) {  // fine-grid pressure q = P p lives on every vertex
         const bool qin = zq && (s_flags & (1u << (16 + j)));
         cp_async(AOS ? dst + 4 * idx + 3 : dst + 3 * TSZ + idx, a.q + (qin ? pb + s_col[j] : 0), sizeof(TS),
                  qin);
@@ -175,6 +175,7 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     }
   };
   auto issue_coef = [&](int kc) {
+    if (MODE == ST_STOKES_B) return;  // no viscous part: the coefficients are not read
     T* dst = cfs + (((kc - zs) & 1) * NT + tid) * 6;
     const bool ok = cube_xy && kc >= 0 && kc < n;
     const T* src = op.coef + (ok ? 6 * (cube_col + kc * n * n) : 0);
@@ -264,7 +265,8 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
     for (int c = 0; c < 3; ++c) {
       eb[c] = ed[c] = ep[c] = TS(0);
       if (inner) {
-        if (MODE == ST_RESID || MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) eb[c] = __ldg(a.b + (c * V + vo));
+        if (MODE == ST_RESID || MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP || MODE == ST_STOKES_B)
+          eb[c] = __ldg(a.b + (c * V + vo));  // STOKES_B: A u
         if (MODE == ST_CHEB_FIRST || MODE == ST_CHEB_STEP) ed[c] = __ldg(a.invD + (c * V + vo));
         if (MODE == ST_CHEB_STEP) ep[c] = a.xprev[c * V + vo];
       }
@@ -366,6 +368,8 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
         }
       } else if constexpr (MODE == ST_STOKES) {
         cube_stokes<T>(Xl, Xh, cf, op.hq, Y);
+      } else if constexpr (MODE == ST_STOKES_B) {
+        cube_stokes_b<T>(Xl, Xh, op.hq, Y);
       } else {
         cube_dca<T, NC>(Xl, Xh, cf, Y);
       }
@@ -438,19 +442,19 @@ __device__ __forceinline__ void stencil_block(const LevelOp<T>& op, const Stenci
           // own vertex value on plane k (CHEB_PRE: x1 = s2 D^-1 b staged in the tile)
           const TS o = inner ? stencil_epilogue<MODE, TS>((TS)Xl[3][c], (TS)yk[c], eb[c], ed[c], ep[c], a.s0, a.s1)
                              : TS(0);
-          if (MODE != ST_STOKES && a.out64)
+          if (MODE != ST_STOKES && MODE != ST_STOKES_B && a.out64)
             a.out64[i] = (double)o;
           else
             a.out[i] = o;
         }
-        if (MODE == ST_STOKES) a.out2[vo] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
+        if (MODE == ST_STOKES || MODE == ST_STOKES_B) a.out2[vo] = (TS)yk[NC - 1];  // (B_f u) on every fine vertex
       }
     }
   };
 
   T Xa[4][NC], Xb[4][NC];
   int rk = 0;
-  if constexpr (sizeof(T) == 4 && MODE != ST_STOKES) {
+  if constexpr (sizeof(T) == 4 && MODE != ST_STOKES && MODE != ST_STOKES_B) {
     // the z-march unrolled by two so that the plane registers alternate roles
     // (no copy of the upper plane into the lower one per layer)
     for (int k = zs; k < z1; k += 2) {
@@ -599,6 +603,13 @@ cudaError_t launch_mode(int mode, const LevelOp<T>& op, const StencilArgs<TS>& a
         AGCA_LAUNCH(ST_STOKES, false);
       }
       break;
+    case ST_STOKES_B:
+      if constexpr (COARSE || sizeof(T) != 8 || sizeof(TS) != 8) {
+        return cudaErrorInvalidValue;
+      } else {
+        AGCA_LAUNCH(ST_STOKES_B, false);
+      }
+      break;
     default: return cudaErrorInvalidValue;
   }
 #undef AGCA_LAUNCH
@@ -710,7 +721,7 @@ cudaError_t launch_stencil(int mode, const LevelOp<T>& op, const StencilArgs<TS>
   const int by = cfg ? cfg->by : 8, zch = cfg ? cfg->zch : 0;
   if constexpr (std::is_same<TS, double>::value && std::is_same<T, double>::value) {
     // FP64 levels run the edge form (their coefficient records exist in FP64 contexts)
-    if (op.hedge && mode != ST_STOKES) return launch_stencil_edge<T>(mode, op, a, s, zch);
+    if (op.hedge && mode != ST_STOKES && mode != ST_STOKES_B) return launch_stencil_edge<T>(mode, op, a, s, zch);
   }
   if constexpr (sizeof(T) == 4 && sizeof(TS) == 4) {
     if (by == 12) {
