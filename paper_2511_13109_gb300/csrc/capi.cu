@@ -989,13 +989,13 @@ agca_status tune_level(agca_ctx* ctx, int l, int reps, std::map<std::string, Til
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // z-chunk candidates: a fixed ladder plus, per block-row count, the chunks
-  // whose block count fills k = 1..8 whole waves of resident blocks (no
+  // whose block count fills k = 1..16 whole waves of resident blocks (no
   // partly filled last wave)
   auto candidates = [&](int by) {
     std::vector<int> zs = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
     const int per_sm = edge ? 2 : (by <= 8 ? 3 : (by <= 12 ? 2 : 1));
     const int per_z = edge ? edge_tiles(lv.n, 1).per_z() : stencil_tiles(lv.n, by, 1).per_z();
-    for (int k = 1; k <= 8; ++k) {
+    for (int k = 1; k <= 16; ++k) {
       const int gz = std::max(1, k * sms * per_sm / per_z);
       zs.push_back((nv + gz - 1) / gz);
     }
