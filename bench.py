@@ -606,6 +606,54 @@ def run_batch(args, dev, stream):
     return out
 
 
+def batch_cycles():
+    """The batch workload's mixed V-cycle batched and one problem at a time,
+    each once inside its own NVTX range (for a launch-list capture) and then
+    timed over 10 cycles with CUDA events; prints one JSON line."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2511_13109_gb300 as pkg
+    from synth import batch_problems
+
+    dev = torch.device("cuda", 0)
+    probs = batch_problems(device=dev)
+    etas = [torch.from_numpy(p.eta).to(dev) for p in probs]
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        b = pkg.Batch([p.N for p in probs], pkg.MIXED, device=dev, stream=s)
+        b.prepare(etas, NU)
+        rs = [torch.rand(3 * c.V[c.L], dtype=torch.float64, device=dev) * 2 - 1 for c in b.contexts]
+        singles = []
+        for p, eta in zip(probs, etas):
+            c = pkg.Context(p.N, pkg.default_levels(p.N), pkg.MIXED, device=dev, stream=s)
+            c.prepare(eta, NU)
+            singles.append(c)
+        for _ in range(3):
+            b.vcycle(rs)
+            for c, r in zip(singles, rs):
+                c.vcycle(r)
+        s.synchronize()
+        for name, run in (("batched", lambda: b.vcycle(rs)),
+                          ("single", lambda: [c.vcycle(r) for c, r in zip(singles, rs)])):
+            torch.cuda.nvtx.range_push(name)
+            run()
+            s.synchronize()
+            torch.cuda.nvtx.range_pop()
+        out = {}
+        for name, run in (("batched_ms", lambda: b.vcycle(rs)),
+                          ("one_by_one_ms", lambda: [c.vcycle(r) for c, r in zip(singles, rs)])):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(10):
+                run()
+            e1.record(s)
+            e1.synchronize()
+            out[name] = e0.elapsed_time(e1) / 10
+    print(json.dumps({"batch_cycles": out, "problems": len(probs)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -624,9 +672,14 @@ def main():
     ap.add_argument("--batch-n", type=int, default=0)
     ap.add_argument("--cycles-only", action="store_true",
                     help="profiling aid: warm-up and timed cycles of both precisions only, one short JSON line")
+    ap.add_argument("--batch-cycles", action="store_true",
+                    help="profiling aid: one batched mixed V-cycle of the 24-problem batch (NVTX range "
+                         "'batched') and the same cycles one by one (range 'single'), then both timed")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_cycles:
+        return batch_cycles()
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
